@@ -1,0 +1,245 @@
+"""Seeded synthetic per-pixel render buffers for the TDM-MIMO cube synthesis.
+
+The paper's frames come from Blender's Cycles renderer (Section II): every pixel of an
+N_az x N_el image carries a range, a strength, an angle of arrival and a velocity
+(the symbol list after Eq. 2).  That renderer and the authors' scene are not
+available, so this module draws buffers with the same structure from numpy's
+``default_rng(seed)``.  It holds none of the method's arithmetic (no phases, no
+sums): it only produces radar parameters and pixel arrays, and it is the one module
+that both the CUDA path and the CPU oracle are fed from.
+
+Conventions
+-----------
+* Pixel p = j * N_az + i for elevation row j and azimuth column i (the render
+  buffers are indexed [el, az] after Eq. 2).
+* Pixel grid is cell-centred: az_i = -60 deg + (i + 1/2) 120 deg / N_az,
+  el_j = -30 deg + (j + 1/2) 60 deg / N_el (the camera angle range stands for the
+  antenna pattern, Section II).
+* sigma is a complex amplitude.  A pixel with sigma == 0 is a background miss and
+  its range is +inf.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, replace
+from typing import Dict, List
+
+import numpy as np
+
+C_LIGHT = 299_792_458.0
+
+
+@dataclass(frozen=True)
+class Radar:
+    """FMCW TDM-MIMO radar parameters (symbols of Eq. 1)."""
+
+    M: int  # Tx antennas
+    N: int  # Rx antennas
+    Ns: int  # fast-time samples per chirp
+    L: int  # TDM blocks (slow time)
+    lam: float = 3.9e-3  # wavelength [m]
+    d_rx: float = 0.0  # Rx spacing [m]; <= 0 means lam / 2
+    mu: float = 30e6 / 1e-6  # chirp slope [Hz/s]
+    fs: float = 10e6  # ADC sampling rate [Hz]
+    t_b: float = 60e-6  # chirp duration [s]
+    t_slow: float = 0.0  # TDM block period [s]; <= 0 means M * t_b
+    c: float = C_LIGHT
+
+    @property
+    def V(self) -> int:
+        return self.M * self.N
+
+    def resolved(self) -> "Radar":
+        """Return a copy with the defaulted fields filled in."""
+        d = self.d_rx if self.d_rx > 0 else self.lam / 2.0
+        t = self.t_slow if self.t_slow > 0 else self.M * self.t_b
+        return replace(self, d_rx=d, t_slow=t)
+
+
+@dataclass
+class Pixels:
+    """Structure-of-arrays render buffers of one frame (flattened [el, az])."""
+
+    range: np.ndarray
+    sigma_re: np.ndarray
+    sigma_im: np.ndarray
+    az: np.ndarray
+    el: np.ndarray
+    vel: np.ndarray
+
+    @property
+    def P(self) -> int:
+        return int(self.range.shape[0])
+
+    @property
+    def dtype(self):
+        return self.range.dtype
+
+    def astype(self, dt) -> "Pixels":
+        return Pixels(*(np.ascontiguousarray(a, dtype=dt) for a in self.arrays()))
+
+    def arrays(self) -> List[np.ndarray]:
+        return [self.range, self.sigma_re, self.sigma_im, self.az, self.el, self.vel]
+
+    def subset(self, idx) -> "Pixels":
+        return Pixels(*(np.ascontiguousarray(a[idx]) for a in self.arrays()))
+
+
+@dataclass
+class Frame:
+    radar: Radar
+    pixels: Pixels
+    out_dtype: str = "complex64"  # "complex64" | "complex128"
+    meta: Dict = field(default_factory=dict)
+
+
+def grid_angles(n_az: int, n_el: int):
+    """Cell-centred az/el grid in radians, flattened with p = j * n_az + i."""
+    az1 = np.deg2rad(-60.0 + (np.arange(n_az) + 0.5) * 120.0 / n_az)
+    el1 = np.deg2rad(-30.0 + (np.arange(n_el) + 0.5) * 60.0 / n_el)
+    az = np.tile(az1, n_el)
+    el = np.repeat(el1, n_az)
+    return az, el
+
+
+def _strength(rng, n, mean=0.0, sd=1.0):
+    mag = np.exp(rng.normal(mean, sd, n))
+    ph = rng.uniform(0.0, 2.0 * np.pi, n)
+    return mag * np.cos(ph), mag * np.sin(ph)
+
+
+def random_frame(radar: Radar, n_az: int, n_el: int, seed: int, mask_frac: float = 0.0,
+                 dtype=np.float32, r_lo=0.5, r_hi=8.0, v_max=2.0) -> Pixels:
+    """Uniform-range random scene on the az/el grid.
+
+    R ~ U(r_lo, r_hi) m, |sigma| = exp(N(0, 1)) with uniform phase, v ~ U(-v_max, v_max)
+    m/s.  A Bernoulli(mask_frac) subset is a background miss: sigma = 0, R = +inf.
+    """
+    rng = np.random.default_rng(seed)
+    P = n_az * n_el
+    az, el = grid_angles(n_az, n_el)
+    rr = rng.uniform(r_lo, r_hi, P)
+    sre, sim = _strength(rng, P)
+    vel = rng.uniform(-v_max, v_max, P)
+    if mask_frac > 0.0:
+        miss = rng.random(P) < mask_frac
+        sre[miss] = 0.0
+        sim[miss] = 0.0
+        rr[miss] = np.inf
+    px = Pixels(rr, sre, sim, az, el, vel)
+    return px.astype(dtype)
+
+
+# ----------------------------------------------------------------------------------
+# The workloads.  Sizes and distributions follow the five synthetic configurations
+# that stand in for the paper's Blender scene (Section III).
+# ----------------------------------------------------------------------------------
+
+def config1(seed: int = 1) -> Frame:
+    """One small frame: M=2, N=4, Ns=64, L=32, 32x32 pixels, FP64 buffers, complex128 out."""
+    radar = Radar(M=2, N=4, Ns=64, L=32)
+    px = random_frame(radar, 32, 32, seed, mask_frac=0.0, dtype=np.float64)
+    return Frame(radar, px, "complex128", {"workload": "frame-32x32-V8-Ns64-L32"})
+
+
+def config2(seed: int = 2) -> Frame:
+    """One frame: M=3, N=4, Ns=256, L=128, 256x256 pixels, 30% background, complex64 out."""
+    radar = Radar(M=3, N=4, Ns=256, L=128)
+    px = random_frame(radar, 256, 256, seed, mask_frac=0.30, dtype=np.float32)
+    return Frame(radar, px, "complex64", {"workload": "frame-256x256-V12-Ns256-L128-mask30"})
+
+
+def parity_frame(seed: int = 11, M=2, N=3, Ns=96, L=48, n_az=71, n_el=70,
+                 mask_frac=0.3, dtype=np.float32) -> Frame:
+    """A mid-size frame whose dimensions are not multiples of any tile (ragged tails)."""
+    radar = Radar(M=M, N=N, Ns=Ns, L=L)
+    px = random_frame(radar, n_az, n_el, seed, mask_frac=mask_frac, dtype=dtype)
+    return Frame(radar, px, "complex64", {"workload": f"parity-{n_az}x{n_el}-V{M*N}-Ns{Ns}-L{L}"})
+
+
+def walking_batch(n_frames: int = 64, seed: int = 4, n_az: int = 256, n_el: int = 256,
+                  dtype=np.float32) -> List[Frame]:
+    """Animation of a walking-pedestrian-like scene in front of a static wall.
+
+    Per frame f: a pedestrian cluster of n_f ~ U{2000..20000} pixels in a contiguous
+    az/el window whose centre moves as 40 deg * sin(2 pi f / 64); its range is
+    R_f + U(-0.3, 0.3) with R_f = 3 + 2 sin(2 pi f / 64 + 0.7) m and its velocity a
+    torso term 1.5 sin(2 pi f / 64) plus a limb term U(-1.5, 1.5), clipped to +-3 m/s.
+    A wall of w_f ~ U{0..45000} pixels sits at R = min(6 / (cos az cos el), 8) m with
+    v = 0 and |sigma| = exp(N(-1, 0.5)).  Everything else is a background miss.
+    """
+    rng = np.random.default_rng(seed)
+    radar = Radar(M=3, N=4, Ns=256, L=128)
+    P = n_az * n_el
+    az, el = grid_angles(n_az, n_el)
+    frames = []
+    for f in range(n_frames):
+        rr = np.full(P, np.inf)
+        sre = np.zeros(P)
+        sim = np.zeros(P)
+        vel = np.zeros(P)
+        # wall: a random set of grid cells not covered by the pedestrian
+        n_ped = int(rng.integers(2000, 20001))
+        n_wall = int(rng.integers(0, 45001))
+        ph = 2.0 * np.pi * f / 64.0
+        az_c = np.deg2rad(40.0 * np.sin(ph))
+        i_c = int(np.clip(np.round((np.rad2deg(az_c) + 60.0) / 120.0 * n_az - 0.5), 0, n_az - 1))
+        # pedestrian window: tall (el) and narrow (az), height:width about 2.5:1
+        w = max(1, int(np.round(np.sqrt(n_ped / 2.5))))
+        h = int(np.ceil(n_ped / w))
+        h = min(h, n_el)
+        w = min(int(np.ceil(n_ped / h)), n_az)
+        i0 = int(np.clip(i_c - w // 2, 0, n_az - w))
+        j0 = int(np.clip(n_el // 2 - h // 2, 0, n_el - h))
+        jj, ii = np.meshgrid(np.arange(j0, j0 + h), np.arange(i0, i0 + w), indexing="ij")
+        ped = (jj * n_az + ii).ravel()[:n_ped]
+        r_f = 3.0 + 2.0 * np.sin(ph + 0.7)
+        rr[ped] = r_f + rng.uniform(-0.3, 0.3, ped.size)
+        vel[ped] = np.clip(1.5 * np.sin(ph) + rng.uniform(-1.5, 1.5, ped.size), -3.0, 3.0)
+        a, b = _strength(rng, ped.size)
+        sre[ped], sim[ped] = a, b
+        free = np.setdiff1d(np.arange(P), ped, assume_unique=True)
+        wall = np.sort(rng.choice(free, size=min(n_wall, free.size), replace=False))
+        rr[wall] = np.minimum(6.0 / (np.cos(az[wall]) * np.cos(el[wall])), 8.0)
+        a, b = _strength(rng, wall.size, mean=-1.0, sd=0.5)
+        sre[wall], sim[wall] = a, b
+        px = Pixels(rr, sre, sim, az.copy(), el.copy(), vel).astype(dtype)
+        frames.append(Frame(radar, px, "complex64",
+                            {"workload": "walking-256x256-V12-Ns256-L128", "frame": f,
+                             "v_torso": 1.5 * np.sin(ph), "n_ped": int(ped.size),
+                             "n_wall": int(wall.size)}))
+    return frames
+
+
+SERVE_CHOICES = dict(M=(2, 3, 4), N=(4, 8, 12), Ns=(128, 256, 512), L=(64, 128, 256),
+                     grid=(64, 128, 256, 512), tier=("fp32", "split_bf16"))
+
+
+def serving_requests(n: int, seed: int = 5, grids=None, tiers=None) -> List[Dict]:
+    """Request mix for the serving loop: uniform choices of radar and image size.
+
+    Each request is a dict with a Radar, a grid edge and an accuracy tier; the pixel
+    buffers are drawn lazily by ``request_frame`` (seed derived from the request id).
+    """
+    rng = np.random.default_rng(seed)
+    grids = grids or SERVE_CHOICES["grid"]
+    tiers = tiers or SERVE_CHOICES["tier"]
+    out = []
+    for k in range(n):
+        radar = Radar(M=int(rng.choice(SERVE_CHOICES["M"])), N=int(rng.choice(SERVE_CHOICES["N"])),
+                      Ns=int(rng.choice(SERVE_CHOICES["Ns"])), L=int(rng.choice(SERVE_CHOICES["L"])))
+        g = int(rng.choice(grids))
+        t = str(rng.choice(tiers))
+        out.append({"id": k, "radar": radar, "grid": g, "tier": t, "seed": seed * 1_000_003 + k})
+    return out
+
+
+def request_frame(req: Dict, dtype=np.float32) -> Frame:
+    px = random_frame(req["radar"], req["grid"], req["grid"], req["seed"], mask_frac=0.30, dtype=dtype)
+    return Frame(req["radar"], px, "complex64", {"workload": "serve", "id": req["id"]})
+
+
+def point_scatterer(radar: Radar, R: float, sigma: complex, az: float, el: float, vel: float,
+                    dtype=np.float64) -> Pixels:
+    """A single-pixel frame holding one point target."""
+    a = lambda x: np.array([x], dtype=dtype)
+    return Pixels(a(R), a(sigma.real), a(sigma.imag), a(az), a(el), a(vel))
