@@ -1,0 +1,264 @@
+/*
+ * rsim.h — C ABI of the GB300 (sm_103a) library for TDM-MIMO FMCW beat-signal
+ * data-cube synthesis from per-pixel render buffers.
+ *
+ * What the library computes (Eq. 1 and Eq. 2 of "A Blender-based channel simulator
+ * for FMCW Radar", Section II), with 0-based n < N_s, l < L and virtual channel
+ * v = m * N + r (Tx m < M, Rx r < N):
+ *
+ *   valid_p       = (sigma_p != 0)                         background misses drop out
+ *   u_p           = cos(el_p) * sin(az_p)                  direction cosine (Eq. 2 AoA)
+ *   R_{p,v}       = R_p + v * d_rx * u_p / 2               path range R_{m,n} (Eq. 1)
+ *   f_D,p         = 2 * vel_p / lambda                     Doppler (Eq. 1, Eq. 2)
+ *   phi(p,v,n,l)  = 2 mu R_{p,v} / c * n / F_s             fast time (Eq. 1)
+ *                 + v * d_rx * u_p / lambda                spatial term (Eq. 2)
+ *                 - f_D,p * l * T_slow                     slow time (Eq. 1)
+ *   cube[v][n][l] = sum over valid p of sigma_p * exp(j 2 pi phi(p,v,n,l))
+ *
+ * Readings where the paper is silent or garbled: T_slow is the TDM block period
+ * (default M * T_b; Eq. 1 steps the phase once per block of M chirps and Eq. 2's
+ * extra "/L" is read as a typo); the sum over m is kept as M*N virtual channels;
+ * d_rx defaults to lambda / 2 (Eq. 2 definitions); sigma is a complex amplitude.
+ *
+ * Conventions for every call:
+ *  - All array pointers are DEVICE pointers owned by the caller, unless a comment
+ *    says otherwise.  The library never frees caller memory; it owns only the
+ *    workspace held by an rsim_ctx.
+ *  - Every call returns an rsim_status; no C++ exception crosses the ABI.  On an
+ *    error, rsim_last_error() returns a message for the calling thread, and the
+ *    contents of output buffers are unspecified.
+ *  - Calls that take a stream are asynchronous on it (they enqueue kernels and
+ *    return).  Checks that need device data (non-finite fields of valid pixels,
+ *    device-side wait limits) set a status word in the context; rsim_sync_status()
+ *    waits for the stream and returns and clears it.
+ *  - Sizes are checked in 64-bit arithmetic; products that overflow give
+ *    RSIM_ERR_OVERFLOW.
+ *  - One rsim_ctx must not be used by two host threads at once, and work enqueued
+ *    through it on one stream must complete before it is reused on another (its
+ *    workspace is shared).  Use one context per stream, or the server below.
+ */
+#ifndef RSIM_H_
+#define RSIM_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream handle (cudaStream_t / CUstream); NULL is the legacy default stream. */
+typedef struct CUstream_st* rsim_stream;
+
+typedef enum {
+  RSIM_OK = 0,
+  RSIM_ERR_INVALID_ARG = 1,  /* NULL pointer, non-positive size, unknown enum value */
+  RSIM_ERR_NONFINITE = 2,    /* a valid pixel has a non-finite field or R <= 0 */
+  RSIM_ERR_OVERFLOW = 3,     /* a size product does not fit in 64 bits / int32 index */
+  RSIM_ERR_OOM = 4,          /* device allocation of the workspace failed */
+  RSIM_ERR_BUDGET = 5,       /* request larger than the configured HBM budget */
+  RSIM_ERR_TIMEOUT = 6,      /* a device-side or host-side wait ran out of time */
+  RSIM_ERR_CANCELLED = 7,    /* a server request was cancelled before it ran */
+  RSIM_ERR_CUDA = 8,         /* a CUDA runtime call failed (message has the detail) */
+  RSIM_ERR_UNSUPPORTED = 9,  /* valid request this build does not handle */
+  RSIM_ERR_NOT_FOUND = 10    /* unknown server ticket */
+} rsim_status;
+
+/* Arithmetic tier of the contraction over pixels. */
+typedef enum {
+  RSIM_TIER_FP32 = 0,       /* FP32 direct sum on CUDA cores */
+  RSIM_TIER_BF16 = 1,       /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
+  RSIM_TIER_SPLIT_BF16 = 2, /* tcgen05, BF16 hi+lo operands (3 products), FP32 accumulate */
+  RSIM_TIER_SPLIT_FP16 = 3, /* tcgen05, FP16 hi+lo operands (3 products), FP32 accumulate */
+  RSIM_TIER_FP16 = 4        /* tcgen05, FP16 operands, FP32 accumulate */
+} rsim_tier;
+
+/* Element type of the pixel arrays (all six share it). */
+enum { RSIM_F32 = 0, RSIM_F64 = 1 };
+/* Element type of the cube: interleaved (re, im) pairs. */
+enum { RSIM_C64 = 0, RSIM_C128 = 1 };
+
+/* Radar parameters (symbols of Eq. 1; SI units). */
+typedef struct {
+  int32_t M;       /* Tx antennas, >= 1 */
+  int32_t N;       /* Rx antennas, >= 1 */
+  int32_t Ns;      /* fast-time samples per chirp, >= 1 */
+  int32_t L;       /* TDM blocks (slow-time samples), >= 1 */
+  double lambda;   /* carrier wavelength [m], > 0 */
+  double d_rx;     /* Rx spacing [m]; <= 0 selects lambda / 2 */
+  double mu;       /* chirp slope [Hz/s] */
+  double fs;       /* fast-time sampling rate [Hz], > 0 */
+  double t_b;      /* chirp duration [s] */
+  double t_slow;   /* TDM block period [s]; <= 0 selects M * t_b */
+  double c;        /* propagation speed [m/s]; <= 0 selects 299792458 */
+} rsim_radar_params;
+
+/* One frame's render buffers: six arrays of P elements, flattened [el][az]
+ * (structure of arrays), all of element type `dtype`.  sigma = (sigma_re, sigma_im)
+ * is the complex amplitude; a pixel with sigma == 0 (either zero sign) is ignored
+ * whatever its other fields hold. */
+typedef struct {
+  int64_t P;
+  int32_t dtype;   /* RSIM_F32 or RSIM_F64 */
+  int32_t reserved;
+  const void* range;    /* R_p [m], > 0 and finite for valid pixels */
+  const void* sigma_re;
+  const void* sigma_im;
+  const void* az;       /* azimuth [rad] */
+  const void* el;       /* elevation [rad] */
+  const void* vel;      /* radial velocity [m/s] (f_D = 2 vel / lambda) */
+} rsim_pixels;
+
+typedef struct rsim_ctx rsim_ctx;
+
+/* Version string of the library (static storage). */
+const char* rsim_version(void);
+
+/* Message of the last error on the calling thread ("" if none); static per thread. */
+const char* rsim_last_error(void);
+
+/* Create a context on `device`.  hbm_budget_bytes bounds the workspace the context
+ * may hold (0 = no bound).  *out receives the context.  Errors: INVALID_ARG, CUDA. */
+rsim_status rsim_create(rsim_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context and free its workspace (waits for the device first).  NULL is a no-op. */
+rsim_status rsim_destroy(rsim_ctx* ctx);
+
+/* Device workspace (bytes) that rsim_synth needs for P pixels with these parameters
+ * and tier.  Host-only computation.  Errors: INVALID_ARG, OVERFLOW. */
+rsim_status rsim_workspace_size(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
+                                rsim_tier tier, size_t* bytes);
+
+/* Synthesise one frame's cube (Eq. 2 summed over all valid pixels).
+ * cube: device buffer of M*N*Ns*L complex values, C-contiguous [M*N][Ns][L],
+ * complex64 (RSIM_C64) or complex128 (RSIM_C128), fully overwritten.  The pixel
+ * buffers are only read.  The context workspace grows if needed (cudaMalloc; the
+ * call then synchronises the device once).  Asynchronous on `stream`.
+ * Errors: INVALID_ARG, OVERFLOW, OOM, BUDGET, CUDA; NONFINITE via rsim_sync_status. */
+rsim_status rsim_synth(rsim_ctx* ctx, const rsim_radar_params* params, const rsim_pixels* pixels,
+                       rsim_tier tier, void* cube, int32_t out_dtype, rsim_stream stream);
+
+/* Synthesise F frames that share one radar configuration in one pass: one launch
+ * per stage over all frames, the contraction as one persistent launch whose work
+ * units (frame, row tile, column tile, pixel split) are taken from a device
+ * counter, longest first.  frames: HOST array of F descriptors; cubes: HOST array
+ * of F device pointers, each laid out as in rsim_synth.  Each frame's result is
+ * bit-identical to rsim_synth of that frame alone with the same tier.
+ * Errors: as rsim_synth. */
+rsim_status rsim_synth_batch(rsim_ctx* ctx, const rsim_radar_params* params,
+                             const rsim_pixels* frames, int32_t F, void* const* cubes,
+                             rsim_tier tier, int32_t out_dtype, rsim_stream stream);
+
+/* Valid-pixel compaction alone (the mask step): idx receives the indices p with
+ * sigma_p != 0 in ascending order (int32, capacity P), *p_valid (DEVICE int64) their
+ * count.  Asynchronous on `stream`. */
+rsim_status rsim_valid_indices(rsim_ctx* ctx, const rsim_pixels* pixels, int32_t* idx,
+                               int64_t* p_valid, rsim_stream stream);
+
+/* Pixel-to-path step alone (FP64): for the q-th valid pixel (ascending p) and channel v,
+ *   a[v*P + q] = 2 mu R_{p,v} / (c F_s)   mod 1, as uint32 units of 2^-32 cycle/sample
+ *   cph[v*P + q] = v d_rx u_p / lambda    mod 1, as uint32 units of 2^-32 cycle
+ *   b[q]       = -f_D,p T_slow            mod 1, as uint32 units of 2^-32 cycle/block
+ *   sigma[2q], sigma[2q+1] = FP32 (re, im) of sigma_p
+ * (rounded to nearest).  a and cph hold V*P uint32, b holds P, sigma 2*P floats;
+ * entries past the valid count are left untouched; *p_valid (DEVICE int64) gets the
+ * count.  Asynchronous on `stream`.  Errors: as rsim_synth. */
+rsim_status rsim_path_phases(rsim_ctx* ctx, const rsim_radar_params* params,
+                             const rsim_pixels* pixels, uint32_t* a, uint32_t* cph, uint32_t* b,
+                             float* sigma, int64_t* p_valid, rsim_stream stream);
+
+/* Wait for `stream`, then return (and clear) the context's device-side status:
+ * RSIM_OK, RSIM_ERR_NONFINITE or RSIM_ERR_TIMEOUT. */
+rsim_status rsim_sync_status(rsim_ctx* ctx, rsim_stream stream);
+
+/* Stage timing for benchmarks.  While profiling is on, every rsim_synth /
+ * rsim_synth_batch call records CUDA events on its stream around its three stages
+ * (compaction + FP64 phases, contraction, split reduction).  rsim_profile_read waits
+ * for the recorded events, returns the summed stage times and launch counts since
+ * profiling was switched on, and starts a new tally. */
+typedef struct {
+  int32_t calls;            /* synth calls recorded */
+  int32_t kernels;          /* kernels those calls launched */
+  double prep_ms;           /* summed device time of the compaction + phase kernels */
+  double contract_ms;       /* summed device time of the contraction kernel */
+  double reduce_ms;         /* summed device time of the split reduction (0 if none) */
+} rsim_profile;
+
+rsim_status rsim_profile_enable(rsim_ctx* ctx, int32_t on);
+rsim_status rsim_profile_read(rsim_ctx* ctx, rsim_profile* out);
+
+/* Kernel-launch plan chosen for a shape (what the autotuner decides). */
+typedef struct {
+  int32_t splits;        /* pixel splits of the contraction (K-split) */
+  int32_t chunk_px;      /* pixels per pipeline stage */
+  int32_t grid;          /* CTAs of the contraction launch */
+  int32_t variant;       /* kernel variant id (tier specific) */
+  int32_t tuned;         /* 1 if chosen by timing, 0 if by the default rule */
+  int32_t reserved[3];
+} rsim_plan;
+
+/* Time candidate plans for (params, P, tier) on `stream` with synthetic pixels and keep
+ * the fastest in the context's cache (and in the JSON file named by the RSIM_TUNE_CACHE
+ * environment variable, if set).  The choice depends on the shape only.  Synchronous.
+ * Errors: as rsim_synth. */
+rsim_status rsim_autotune(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
+                          rsim_tier tier, rsim_plan* chosen, rsim_stream stream);
+
+/* The plan rsim_synth would use now for (params, P, tier).  Host only. */
+rsim_status rsim_get_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
+                          rsim_tier tier, rsim_plan* plan);
+
+/* ----------------------------------------------------------------------------------
+ * Serving: continuous batching of cube-synthesis requests.
+ *
+ * A server owns `slots` CUDA streams, each with its own workspace.  submit() queues a
+ * request (FIFO); a host scheduler thread admits the head request as soon as a slot is
+ * free and its workspace fits in the HBM budget still unreserved, and launches it on
+ * that slot's stream, so requests that arrive while others run start as soon as
+ * resources free up and their kernels overlap on the device.  Completion is detected
+ * with CUDA events; latency is measured from submit() to completion.
+ * ---------------------------------------------------------------------------------- */
+typedef struct rsim_server rsim_server;
+
+typedef struct {
+  int32_t slots;             /* concurrent requests on the device (>= 1) */
+  int32_t max_queue;         /* queued requests accepted before submit() refuses (BUDGET) */
+  size_t hbm_budget_bytes;   /* bound on the sum of admitted workspaces (0 = no bound) */
+} rsim_server_opts;
+
+typedef struct {
+  rsim_radar_params params;
+  rsim_pixels pixels;        /* device buffers; must stay valid until the request completes */
+  rsim_tier tier;
+  int32_t out_dtype;
+  void* cube;                /* device output, as in rsim_synth */
+} rsim_request;
+
+typedef struct {
+  uint64_t submitted, completed, cancelled, failed;
+  double p50_ms, p99_ms, mean_ms, max_ms;   /* submit -> completion latency */
+  double busy_s;                            /* wall time from first submit to last completion */
+  double path_samples;                      /* sum over completed of P_valid * V * N_s * L */
+  size_t peak_reserved_bytes;               /* largest sum of admitted workspaces seen */
+  int32_t peak_in_flight;                   /* largest number of concurrently running requests */
+  int32_t reserved;
+} rsim_server_stats;
+
+rsim_status rsim_server_create(rsim_ctx* ctx, const rsim_server_opts* opts, rsim_server** out);
+/* Queue a request; *ticket identifies it.  Errors: INVALID_ARG (bad request),
+ * BUDGET (workspace larger than the whole budget, or queue full). */
+rsim_status rsim_server_submit(rsim_server* s, const rsim_request* req, uint64_t* ticket);
+/* Wait up to timeout_ms (< 0: no limit) for a ticket.  Returns the request's status
+ * (OK, NONFINITE, CUDA, CANCELLED), TIMEOUT if it has not finished, NOT_FOUND if
+ * the ticket is unknown or already collected.  A finished ticket is collected once. */
+rsim_status rsim_server_wait(rsim_server* s, uint64_t ticket, int32_t timeout_ms);
+/* Cancel a request that has not been admitted yet (running requests complete). */
+rsim_status rsim_server_cancel(rsim_server* s, uint64_t ticket);
+rsim_status rsim_server_stats_get(rsim_server* s, rsim_server_stats* out);
+/* Stop the scheduler, wait for running requests, free slot workspaces. */
+rsim_status rsim_server_destroy(rsim_server* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RSIM_H_ */

@@ -1,0 +1,290 @@
+"""ctypes binding of librsim (include/rsim.h): same names, argument marshalling only.
+
+Tensors are PyTorch device tensors; their data pointers and the current CUDA stream
+are passed through unchanged.  Every function raises ``RsimError`` on a non-OK status.
+There is no fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import (POINTER, Structure, c_char_p, c_double, c_int, c_int32, c_int64, c_size_t,
+                    c_uint64, c_void_p)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "librsim.so")
+
+OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_OVERFLOW, ERR_OOM, ERR_BUDGET, ERR_TIMEOUT, \
+    ERR_CANCELLED, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOT_FOUND = range(11)
+STATUS_NAMES = ["OK", "INVALID_ARG", "NONFINITE", "OVERFLOW", "OOM", "BUDGET", "TIMEOUT",
+                "CANCELLED", "CUDA", "UNSUPPORTED", "NOT_FOUND"]
+TIER_FP32, TIER_BF16, TIER_SPLIT_BF16, TIER_SPLIT_FP16, TIER_FP16 = range(5)
+TIERS = {"fp32": TIER_FP32, "bf16": TIER_BF16, "split_bf16": TIER_SPLIT_BF16,
+         "split_fp16": TIER_SPLIT_FP16, "fp16": TIER_FP16}
+F32, F64 = 0, 1
+C64, C128 = 0, 1
+
+
+class RsimError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"rsim status {STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class rsim_radar_params(Structure):
+    _fields_ = [("M", c_int32), ("N", c_int32), ("Ns", c_int32), ("L", c_int32),
+                ("lambda_", c_double), ("d_rx", c_double), ("mu", c_double), ("fs", c_double),
+                ("t_b", c_double), ("t_slow", c_double), ("c", c_double)]
+
+
+class rsim_pixels(Structure):
+    _fields_ = [("P", c_int64), ("dtype", c_int32), ("reserved", c_int32),
+                ("range", c_void_p), ("sigma_re", c_void_p), ("sigma_im", c_void_p),
+                ("az", c_void_p), ("el", c_void_p), ("vel", c_void_p)]
+
+
+class rsim_plan(Structure):
+    _fields_ = [("splits", c_int32), ("chunk_px", c_int32), ("grid", c_int32),
+                ("variant", c_int32), ("tuned", c_int32), ("reserved", c_int32 * 3)]
+
+
+class rsim_server_opts(Structure):
+    _fields_ = [("slots", c_int32), ("max_queue", c_int32), ("hbm_budget_bytes", c_size_t)]
+
+
+class rsim_request(Structure):
+    _fields_ = [("params", rsim_radar_params), ("pixels", rsim_pixels), ("tier", c_int32),
+                ("out_dtype", c_int32), ("cube", c_void_p)]
+
+
+class rsim_server_stats(Structure):
+    _fields_ = [("submitted", c_uint64), ("completed", c_uint64), ("cancelled", c_uint64),
+                ("failed", c_uint64), ("p50_ms", c_double), ("p99_ms", c_double),
+                ("mean_ms", c_double), ("max_ms", c_double), ("busy_s", c_double),
+                ("path_samples", c_double), ("peak_reserved_bytes", c_size_t),
+                ("peak_in_flight", c_int32), ("reserved", c_int32)]
+
+
+class rsim_profile(Structure):
+    _fields_ = [("calls", c_int32), ("kernels", c_int32), ("prep_ms", c_double),
+                ("contract_ms", c_double), ("reduce_ms", c_double)]
+
+
+# name -> (restype, argtypes); the full exported surface of include/rsim.h
+SIGNATURES = {
+    "rsim_version": (c_char_p, []),
+    "rsim_last_error": (c_char_p, []),
+    "rsim_create": (c_int, [POINTER(c_void_p), c_int, c_size_t]),
+    "rsim_destroy": (c_int, [c_void_p]),
+    "rsim_workspace_size": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
+                                    POINTER(c_size_t)]),
+    "rsim_synth": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels), c_int,
+                           c_void_p, c_int32, c_void_p]),
+    "rsim_synth_batch": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels),
+                                 c_int32, POINTER(c_void_p), c_int, c_int32, c_void_p]),
+    "rsim_valid_indices": (c_int, [c_void_p, POINTER(rsim_pixels), c_void_p, c_void_p, c_void_p]),
+    "rsim_path_phases": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels),
+                                 c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "rsim_sync_status": (c_int, [c_void_p, c_void_p]),
+    "rsim_autotune": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
+                              POINTER(rsim_plan), c_void_p]),
+    "rsim_profile_enable": (c_int, [c_void_p, c_int32]),
+    "rsim_profile_read": (c_int, [c_void_p, POINTER(rsim_profile)]),
+    "rsim_get_plan": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
+                              POINTER(rsim_plan)]),
+    "rsim_server_create": (c_int, [c_void_p, POINTER(rsim_server_opts), POINTER(c_void_p)]),
+    "rsim_server_submit": (c_int, [c_void_p, POINTER(rsim_request), POINTER(c_uint64)]),
+    "rsim_server_wait": (c_int, [c_void_p, c_uint64, c_int32]),
+    "rsim_server_cancel": (c_int, [c_void_p, c_uint64]),
+    "rsim_server_stats_get": (c_int, [c_void_p, POINTER(rsim_server_stats)]),
+    "rsim_server_destroy": (c_int, [c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load librsim.so (built by ``build.build()``) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"librsim.so is not built ({path}); run paper_2307_09226_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def last_error() -> str:
+    return load().rsim_last_error().decode()
+
+
+def check(status: int):
+    if status != OK:
+        raise RsimError(status, last_error())
+    return status
+
+
+def radar_params(radar) -> rsim_radar_params:
+    """Marshal a ``synth.Radar`` (or anything with the same attributes)."""
+    return rsim_radar_params(int(radar.M), int(radar.N), int(radar.Ns), int(radar.L),
+                             float(radar.lam), float(radar.d_rx), float(radar.mu), float(radar.fs),
+                             float(radar.t_b), float(radar.t_slow), float(radar.c))
+
+
+def pixels_struct(t) -> rsim_pixels:
+    """Marshal a dict/tuple of six equal-length contiguous device tensors
+    (range, sigma_re, sigma_im, az, el, vel) of float32 or float64."""
+    import torch
+    arrs = [t[k] for k in ("range", "sigma_re", "sigma_im", "az", "el", "vel")] if isinstance(t, dict) else list(t)
+    P = int(arrs[0].numel())
+    dt = arrs[0].dtype
+    for a in arrs:
+        if a.dtype != dt or a.numel() != P or not a.is_contiguous():
+            raise ValueError("pixel arrays must be contiguous and share dtype and length")
+    if dt == torch.float32:
+        code = F32
+    elif dt == torch.float64:
+        code = F64
+    else:
+        raise ValueError("pixel arrays must be float32 or float64")
+    return rsim_pixels(P, code, 0, *[a.data_ptr() for a in arrs])
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return c_void_p(s.cuda_stream)
+
+
+def _ptr(x):
+    return None if x is None else c_void_p(x.data_ptr())
+
+
+# ---------------------------------------------------------------------------------
+# Thin wrappers with the C names.
+# ---------------------------------------------------------------------------------
+
+def rsim_version() -> str:
+    return load().rsim_version().decode()
+
+
+def rsim_create(device: int = 0, hbm_budget_bytes: int = 0) -> c_void_p:
+    h = c_void_p()
+    check(load().rsim_create(ctypes.byref(h), int(device), int(hbm_budget_bytes)))
+    return h
+
+
+def rsim_destroy(ctx):
+    check(load().rsim_destroy(ctx))
+
+
+def rsim_workspace_size(ctx, radar, P: int, tier: int) -> int:
+    out = c_size_t()
+    check(load().rsim_workspace_size(ctx, ctypes.byref(radar_params(radar)), int(P), int(tier),
+                                     ctypes.byref(out)))
+    return int(out.value)
+
+
+def rsim_synth(ctx, radar, pixels, tier: int, cube, stream=None):
+    """cube: complex64 or complex128 device tensor of shape [M*N, Ns, L]."""
+    import torch
+    od = C128 if cube.dtype == torch.complex128 else C64
+    if cube.dtype not in (torch.complex64, torch.complex128) or not cube.is_contiguous():
+        raise ValueError("cube must be a contiguous complex64/complex128 tensor")
+    px = pixels if isinstance(pixels, rsim_pixels) else pixels_struct(pixels)
+    check(load().rsim_synth(ctx, ctypes.byref(radar_params(radar)), ctypes.byref(px), int(tier),
+                            _ptr(cube), od, _stream(stream)))
+
+
+def rsim_synth_batch(ctx, radar, frames, tier: int, cubes, stream=None):
+    import torch
+    F = len(frames)
+    arr = (rsim_pixels * F)(*[f if isinstance(f, rsim_pixels) else pixels_struct(f) for f in frames])
+    ptrs = (c_void_p * F)(*[c.data_ptr() for c in cubes])
+    od = C128 if cubes[0].dtype == torch.complex128 else C64
+    check(load().rsim_synth_batch(ctx, ctypes.byref(radar_params(radar)), arr, F, ptrs, int(tier), od,
+                                  _stream(stream)))
+
+
+def rsim_valid_indices(ctx, pixels, idx, p_valid, stream=None):
+    px = pixels if isinstance(pixels, rsim_pixels) else pixels_struct(pixels)
+    check(load().rsim_valid_indices(ctx, ctypes.byref(px), _ptr(idx), _ptr(p_valid), _stream(stream)))
+
+
+def rsim_path_phases(ctx, radar, pixels, a, cph, b, sigma, p_valid, stream=None):
+    px = pixels if isinstance(pixels, rsim_pixels) else pixels_struct(pixels)
+    check(load().rsim_path_phases(ctx, ctypes.byref(radar_params(radar)), ctypes.byref(px), _ptr(a),
+                                  _ptr(cph), _ptr(b), _ptr(sigma), _ptr(p_valid), _stream(stream)))
+
+
+def rsim_sync_status(ctx, stream=None) -> int:
+    """Returns the status code (does not raise) so callers can test for NONFINITE."""
+    return int(load().rsim_sync_status(ctx, _stream(stream)))
+
+
+def rsim_autotune(ctx, radar, P: int, tier: int, stream=None) -> rsim_plan:
+    plan = rsim_plan()
+    check(load().rsim_autotune(ctx, ctypes.byref(radar_params(radar)), int(P), int(tier),
+                               ctypes.byref(plan), _stream(stream)))
+    return plan
+
+
+def rsim_profile_enable(ctx, on: bool):
+    check(load().rsim_profile_enable(ctx, 1 if on else 0))
+
+
+def rsim_profile_read(ctx) -> rsim_profile:
+    p = rsim_profile()
+    check(load().rsim_profile_read(ctx, ctypes.byref(p)))
+    return p
+
+
+def rsim_get_plan(ctx, radar, P: int, tier: int) -> rsim_plan:
+    plan = rsim_plan()
+    check(load().rsim_get_plan(ctx, ctypes.byref(radar_params(radar)), int(P), int(tier),
+                               ctypes.byref(plan)))
+    return plan
+
+
+def rsim_server_create(ctx, slots=4, max_queue=4096, hbm_budget_bytes=0) -> c_void_p:
+    h = c_void_p()
+    opts = rsim_server_opts(int(slots), int(max_queue), int(hbm_budget_bytes))
+    check(load().rsim_server_create(ctx, ctypes.byref(opts), ctypes.byref(h)))
+    return h
+
+
+def make_request(radar, pixels, tier, cube) -> rsim_request:
+    import torch
+    px = pixels if isinstance(pixels, rsim_pixels) else pixels_struct(pixels)
+    od = C128 if cube.dtype == torch.complex128 else C64
+    return rsim_request(radar_params(radar), px, int(tier), od, c_void_p(cube.data_ptr()))
+
+
+def rsim_server_submit(server, req: rsim_request) -> int:
+    t = c_uint64()
+    check(load().rsim_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return int(t.value)
+
+
+def rsim_server_wait(server, ticket: int, timeout_ms: int = -1) -> int:
+    """Returns the request's status code (does not raise)."""
+    return int(load().rsim_server_wait(server, c_uint64(ticket), int(timeout_ms)))
+
+
+def rsim_server_cancel(server, ticket: int) -> int:
+    return int(load().rsim_server_cancel(server, c_uint64(ticket)))
+
+
+def rsim_server_stats_get(server) -> rsim_server_stats:
+    s = rsim_server_stats()
+    check(load().rsim_server_stats_get(server, ctypes.byref(s)))
+    return s
+
+
+def rsim_server_destroy(server):
+    check(load().rsim_server_destroy(server))

@@ -1,0 +1,217 @@
+// FP32 direct sum of Eq. 2 on CUDA cores, and the ordered split reduction.
+//
+// The phase of Eq. 2 separates into a fast-time/channel part a_{p,v} n + c_{p,v} and a
+// slow-time part b_p l, so each cube entry is
+//     cube[v][n][l] = sum_q G_v[q][n] * D[q][l],
+//     G_v[q][n] = exp(j 2 pi (a_{q,v} n + c_{q,v})),   D[q][l] = sigma_q exp(j 2 pi b_q l),
+// over the compacted valid pixels q.  A CTA owns a 64 (n) x 64 (l) tile of one
+// channel and one contiguous split of the pixels; per 32-pixel chunk it writes the
+// chunk's phasors to shared memory (phases are exact 32-bit fixed-point products,
+// so only a phase in [-1/2, 1/2) cycle is ever converted to float) and then every
+// thread accumulates a 4 x 4 block of complex outputs with 4 FFMA per term.
+#include <algorithm>
+
+#include "rsim_internal.h"
+
+namespace rsim {
+namespace {
+
+constexpr int kTN = 64;       // n per tile
+constexpr int kTL = 64;       // l per tile
+constexpr int kThreads = 256;
+
+// exp(j 2 pi x) for a 2^-32-cycle fixed-point phase.  The phase is reinterpreted as
+// a signed fraction in [-1/2, 1/2) cycle, so the argument of the hardware sine and
+// cosine is within [-pi, pi), where their absolute error is below 2^-21.
+__device__ __forceinline__ float2 cis_q32(uint32_t ph) {
+  const float ang = (float)(int32_t)ph * 1.46291807926715968e-09f;  // 2 pi / 2^32
+  float s, c;
+  __sincosf(ang, &s, &c);
+  return make_float2(c, s);
+}
+
+__device__ __forceinline__ void cmac(float2& acc, float2 g, float2 d) {
+  acc.x = fmaf(g.x, d.x, acc.x);
+  acc.x = fmaf(-g.y, d.y, acc.x);
+  acc.y = fmaf(g.x, d.y, acc.y);
+  acc.y = fmaf(g.y, d.x, acc.y);
+}
+
+__global__ void __launch_bounds__(kThreads)
+direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_per_frame,
+           int out_dtype) {
+  const int f = blockIdx.x / units_per_frame;
+  int r = blockIdx.x % units_per_frame;
+  const FrameIO& fr = frames[f];
+  const int s = r % splits;
+  r /= splits;
+  const int ntl = (k.L + kTL - 1) / kTL;
+  const int ntn = (k.Ns + kTN - 1) / kTN;
+  const int tl_i = r % ntl;
+  r /= ntl;
+  const int tn_i = r % ntn;
+  const int v = r / ntn;
+  const int n0 = tn_i * kTN, l0 = tl_i * kTL;
+
+  const int64_t pv = (int64_t)fr.meta[0];
+  const int64_t nch = (pv + kChunkPx - 1) / kChunkPx;
+  const int64_t c0 = nch * s / splits, c1 = nch * (s + 1) / splits;
+
+  __shared__ float2 Gs[kChunkPx][kTN];
+  __shared__ float2 Ds[kChunkPx][kTL];
+
+  const int tid = threadIdx.x;
+  const int tn = tid >> 4, tl = tid & 15;  // rows tn*4 .. +3 ; cols tl + 16 j
+  float2 acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
+
+  const uint32_t* pA = fr.phA + (int64_t)v * fr.Pcap;
+  const uint32_t* pC = fr.phC + (int64_t)v * fr.Pcap;
+
+  for (int64_t c = c0; c < c1; ++c) {
+    const int64_t q0 = c * kChunkPx;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < (kChunkPx * kTN) / kThreads; ++i) {
+      const int e = tid + i * kThreads;
+      const int qq = e / kTN, nn = e % kTN;
+      const int64_t q = q0 + qq;
+      const int n = n0 + nn;
+      float2 g = make_float2(0.f, 0.f);
+      if (q < pv && n < k.Ns) g = cis_q32(pA[q] * (uint32_t)n + pC[q]);
+      Gs[qq][nn] = g;
+    }
+#pragma unroll
+    for (int i = 0; i < (kChunkPx * kTL) / kThreads; ++i) {
+      const int e = tid + i * kThreads;
+      const int qq = e / kTL, ll = e % kTL;
+      const int64_t q = q0 + qq;
+      const int l = l0 + ll;
+      float2 d = make_float2(0.f, 0.f);
+      if (q < pv && l < k.L) {
+        const float2 w = cis_q32(fr.phB[q] * (uint32_t)l);
+        const float2 sg = fr.sig[q];
+        d = make_float2(sg.x * w.x - sg.y * w.y, sg.x * w.y + sg.y * w.x);
+      }
+      Ds[qq][ll] = d;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int qq = 0; qq < kChunkPx; ++qq) {
+      const float4 ga = *reinterpret_cast<const float4*>(&Gs[qq][tn * 4]);
+      const float4 gb = *reinterpret_cast<const float4*>(&Gs[qq][tn * 4 + 2]);
+      const float2 g[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w),
+                           make_float2(gb.x, gb.y), make_float2(gb.z, gb.w)};
+      float2 d[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) d[j] = Ds[qq][tl + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cmac(acc[i][j], g[i], d[j]);
+    }
+  }
+
+  // write the tile: final cube when there is one split, else this split's partial
+  const int64_t rows = (int64_t)k.V * k.Ns;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int n = n0 + tn * 4 + i;
+    if (n >= k.Ns) continue;
+    const int64_t row = (int64_t)v * k.Ns + n;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int l = l0 + tl + 16 * j;
+      if (l >= k.L) continue;
+      const int64_t o = row * k.L + l;
+      if (splits == 1) {
+        if (out_dtype == RSIM_C128)
+          reinterpret_cast<double2*>(fr.cube)[o] = make_double2(acc[i][j].x, acc[i][j].y);
+        else
+          reinterpret_cast<float2*>(fr.cube)[o] = acc[i][j];
+      } else {
+        fr.partial[(int64_t)s * rows * k.L + o] = acc[i][j];
+      }
+    }
+  }
+}
+
+// cube = scale * sum over splits s = 0, 1, ... (in this order, FP64) of partial[s].
+__global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, int splits,
+                             int out_dtype, int scale_mode) {
+  const FrameIO& fr = frames[blockIdx.y];
+  double scale = 1.0;
+  if (scale_mode) {
+    const float m = __uint_as_float((unsigned)fr.meta[1]);
+    scale = (m > 0.f) ? ldexp(1.0, ilogbf(m) + 1) : 1.0;
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < splits; ++s) {
+      const float2 p = fr.partial[(int64_t)s * count + i];
+      re += (double)p.x;
+      im += (double)p.y;
+    }
+    re *= scale;
+    im *= scale;
+    if (out_dtype == RSIM_C128)
+      reinterpret_cast<double2*>(fr.cube)[i] = make_double2(re, im);
+    else
+      reinterpret_cast<float2*>(fr.cube)[i] = make_float2((float)re, (float)im);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits,
+                          int out_dtype, cudaStream_t st) {
+  const int ntn = (k.Ns + kTN - 1) / kTN, ntl = (k.L + kTL - 1) / kTL;
+  const int64_t upf = (int64_t)k.V * ntn * ntl * splits;
+  const int64_t blocks = upf * F;
+  if (blocks <= 0) return cudaSuccess;
+  if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
+  direct_sum<<<(unsigned)blocks, kThreads, 0, st>>>(frames, k, splits, (int)upf, out_dtype);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
+                          float scale_mode, cudaStream_t st) {
+  const int64_t count = (int64_t)k.V * k.Ns * k.L;
+  if (count <= 0 || F <= 0) return cudaSuccess;
+  int64_t blocks = (count + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  dim3 grid((unsigned)blocks, F);
+  split_reduce<<<grid, 256, 0, st>>>(frames, count, splits, out_dtype, scale_mode != 0.f ? 1 : 0);
+  return cudaGetLastError();
+}
+
+int units_per_split(int tier, int V, int Ns, int L) {
+  if (tier == RSIM_TIER_FP32) return V * ((Ns + kTN - 1) / kTN) * ((L + kTL - 1) / kTL);
+  const int64_t rows = (int64_t)V * Ns;
+  const int nt = (L + 127) / 128;
+  return (int)(((rows + 127) / 128) * nt);
+}
+
+int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms) {
+  const int tiles = units_per_split(tier, V, Ns, L);
+  const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
+  // FP32: about 4 resident CTAs per SM; tensor tiers: one persistent CTA per SM.
+  const int64_t target = (tier == RSIM_TIER_FP32) ? 4ll * num_sms : (int64_t)num_sms;
+  int64_t s = (target + tiles - 1) / tiles;
+  // keep at least 8 chunks (256 pixels) per split
+  const int64_t smax = chunks / 8 > 0 ? chunks / 8 : 1;
+  if (s > smax) s = smax;
+  // FP32 accumulation: at most 8192 pixels per split, so that the running sum of
+  // random-phase terms keeps a relative rounding error of a few 1e-6 (the splits are
+  // then added in FP64)
+  if (tier == RSIM_TIER_FP32) s = std::max<int64_t>(s, (P + 8191) / 8192);
+  if (s > kMaxSplits) s = kMaxSplits;
+  if (s < 1) s = 1;
+  return (int)s;
+}
+
+}  // namespace rsim

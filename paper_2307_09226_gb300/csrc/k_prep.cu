@@ -1,0 +1,178 @@
+// Valid-pixel compaction (mask step) and FP64 pixel-to-path phases.
+//
+// A pixel is a point target (Section II, the text before Eq. 2); one with zero
+// strength is a background miss and is dropped.  The kept pixels are stored in
+// ascending pixel order, together with the quantities Eq. 1 / Eq. 2 need per
+// (pixel, virtual channel): the fast-time phase increment 2 mu R_{p,v} / (c F_s),
+// the spatial phase v d_rx u_p / lambda and the slow-time increment -f_D T_slow.
+// They are computed in FP64 and range-reduced to fractions of a cycle held as
+// 32-bit fixed point (2^-32 cycle units), so that a phase at sample n is the exact
+// integer product a * n mod 2^32: no phase of tens of cycles is ever formed in FP32.
+//
+// Two kernels, one grid row per frame:
+//   prep_count   - valid pixels per 1024-pixel tile;
+//   prep_scatter - tile offset = sum of earlier tile counts, ordered in-tile rank by
+//                  warp ballots, then writes the index and the path phases.
+// Both are deterministic (no atomics decide positions).
+#include <math.h>
+
+#include "rsim_internal.h"
+
+namespace rsim {
+namespace {
+
+template <typename T>
+__device__ __forceinline__ bool is_valid(const T* sre, const T* sim, int64_t p) {
+  return (sre[p] != T(0)) || (sim[p] != T(0));
+}
+
+// frac(x) as an unsigned 64-bit fixed-point number of 2^-64 units, rounded to nearest.
+__device__ __forceinline__ uint64_t frac_u64(double x) {
+  double f = x - floor(x);  // exact for |x| < 2^52; in [0, 1]
+  if (!(f < 1.0)) f = 0.0;  // x = -tiny can give f == 1.0
+  return __double2ull_rn(f * 18446744073709551616.0);
+}
+
+// Round a 2^-64 fixed-point fraction to the nearest 2^-32 unit (mod 1).
+__device__ __forceinline__ uint32_t top32(uint64_t x) {
+  return (uint32_t)((x + 0x80000000ull) >> 32);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPrepThreads) prep_count(const FrameIO* __restrict__ frames) {
+  const FrameIO& fr = frames[blockIdx.y];
+  const int64_t base = (int64_t)blockIdx.x * kPrepTile;
+  if (base >= fr.P) return;
+  const T* sre = (const T*)fr.sre;
+  const T* sim = (const T*)fr.sim;
+  int cnt = 0;
+  for (int i = threadIdx.x; i < kPrepTile; i += kPrepThreads) {
+    int64_t p = base + i;
+    if (p < fr.P && is_valid(sre, sim, p)) ++cnt;
+  }
+  // block sum
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  __shared__ int ws[kPrepThreads / 32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < kPrepThreads / 32; ++w) s += ws[w];
+    fr.blk_count[blockIdx.x] = s;
+    if (blockIdx.x == 0) fr.meta[1] = 0ull;  // max |sigma| accumulator, filled by prep_scatter
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPrepThreads)
+prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigned* status) {
+  const FrameIO& fr = frames[blockIdx.y];
+  const int64_t base = (int64_t)blockIdx.x * kPrepTile;
+  if (base >= fr.P) return;
+  const int nblk = (int)((fr.P + kPrepTile - 1) / kPrepTile);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kWarps = kPrepThreads / 32;
+  __shared__ long long s_off;
+  __shared__ int s_warp[kWarps];
+  __shared__ float s_max[kWarps];
+
+  // offset of this tile = sum of the counts of earlier tiles (fixed order)
+  long long part = 0;
+  for (int b = tid; b < (int)blockIdx.x; b += kPrepThreads) part += fr.blk_count[b];
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if (lane == 0) s_warp[warp] = (int)part;  // each partial < 2^31 (P < 2^31 checked on host)
+  __syncthreads();
+  if (tid == 0) {
+    long long s = 0;
+    for (int w = 0; w < kWarps; ++w) s += s_warp[w];
+    s_off = s;
+  }
+  __syncthreads();
+  long long off = s_off;
+
+  const T* R = (const T*)fr.range;
+  const T* sre = (const T*)fr.sre;
+  const T* sim = (const T*)fr.sim;
+  const T* az = (const T*)fr.az;
+  const T* el = (const T*)fr.el;
+  const T* vel = (const T*)fr.vel;
+  float mymax = 0.f;
+
+  for (int row = 0; row < kPrepTile / kPrepThreads; ++row) {
+    const int64_t p = base + (int64_t)row * kPrepThreads + tid;
+    const bool v = (p < fr.P) && is_valid(sre, sim, p);
+    const unsigned bal = __ballot_sync(0xffffffffu, v);
+    __syncthreads();  // s_warp reuse
+    if (lane == 0) s_warp[warp] = __popc(bal);
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      int c = s_warp[w];
+      before += (w < warp) ? c : 0;
+      total += c;
+    }
+    const long long q = off + before + __popc(bal & ((1u << lane) - 1u));
+    if (v) {
+      fr.idx[q] = (int32_t)p;
+      if (!idx_only) {
+        const double r = (double)R[p], a = (double)az[p], e = (double)el[p], w = (double)vel[p];
+        double s_re = (double)sre[p], s_im = (double)sim[p];
+        const bool ok = isfinite(r) && r > 0.0 && isfinite(a) && isfinite(e) && isfinite(w) &&
+                        isfinite(s_re) && isfinite(s_im);
+        uint64_t A0 = 0, dA = 0, G = 0, Bq = 0;
+        if (ok) {
+          const double u = cos(e) * sin(a);       // direction cosine
+          A0 = frac_u64(k.k_a0 * r);              // 2 mu R_p / (c F_s)
+          dA = frac_u64(k.k_da * u);              // mu d_rx u / (c F_s): per channel index
+          G = frac_u64(k.k_g * u);                // d_rx u / lambda: per channel index
+          Bq = frac_u64(k.k_b * w);               // -2 vel T_slow / lambda
+        } else {
+          atomicOr(status, kStatusNonfinite);
+          s_re = 0.0;
+          s_im = 0.0;
+        }
+        for (int ch = 0; ch < k.V; ++ch) {
+          const uint64_t vv = (uint64_t)ch;
+          fr.phA[(int64_t)ch * fr.Pcap + q] = top32(A0 + vv * dA);
+          fr.phC[(int64_t)ch * fr.Pcap + q] = top32(vv * G);
+        }
+        fr.phB[q] = top32(Bq);
+        const float fr_re = (float)s_re, fr_im = (float)s_im;
+        fr.sig[q] = make_float2(fr_re, fr_im);
+        mymax = fmaxf(mymax, fmaxf(fabsf(fr_re), fabsf(fr_im)));
+      }
+    }
+    off += total;
+  }
+  if (blockIdx.x == nblk - 1 && tid == 0) fr.meta[0] = (unsigned long long)off;
+  if (!idx_only) {
+    for (int o = 16; o > 0; o >>= 1) mymax = fmaxf(mymax, __shfl_xor_sync(0xffffffffu, mymax, o));
+    __syncthreads();
+    if (lane == 0) s_max[warp] = mymax;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.f;
+      for (int w = 0; w < kWarps; ++w) m = fmaxf(m, s_max[w]);
+      if (m > 0.f) atomicMax(&fr.meta[1], (unsigned long long)__float_as_uint(m));
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_prep(const Consts& k, const FrameIO* frames, int F, int64_t maxP, int dtype,
+                        bool idx_only, unsigned* status, cudaStream_t st) {
+  if (F <= 0 || maxP <= 0) return cudaSuccess;
+  const int nblk = (int)((maxP + kPrepTile - 1) / kPrepTile);
+  dim3 grid(nblk, F);
+  if (dtype == RSIM_F64) {
+    prep_count<double><<<grid, kPrepThreads, 0, st>>>(frames);
+    prep_scatter<double><<<grid, kPrepThreads, 0, st>>>(frames, k, idx_only ? 1 : 0, status);
+  } else {
+    prep_count<float><<<grid, kPrepThreads, 0, st>>>(frames);
+    prep_scatter<float><<<grid, kPrepThreads, 0, st>>>(frames, k, idx_only ? 1 : 0, status);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rsim

@@ -1,0 +1,494 @@
+// C ABI of librsim: argument checks, context and workspace, plan choice and the
+// stage sequence of one synthesis (compaction + FP64 phases -> contraction ->
+// ordered split reduction).  Declarations and contracts are in include/rsim.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rsim_ctx.h"
+#include "rsim_internal.h"
+
+namespace rsim {
+
+thread_local std::string g_last_error;
+
+rsim_status fail(rsim_status st, const std::string& msg) {
+  g_last_error = msg;
+  return st;
+}
+
+rsim_status cuda_fail(cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(RSIM_ERR_CUDA, m);
+}
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// overflow-checked a * b for non-negative 64-bit values
+static bool mul_ok(int64_t a, int64_t b, int64_t* out) {
+  if (a < 0 || b < 0) return false;
+  if (a != 0 && b > INT64_MAX / a) return false;
+  *out = a * b;
+  return true;
+}
+
+FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, size_t base) {
+  FrameLayout fl{};
+  const int64_t Pcap = std::max<int64_t>(64, (P + 63) / 64 * 64);
+  fl.Pcap = Pcap;
+  size_t o = align_up(base, 256);
+  fl.idx = o;      o = align_up(o + 4 * (size_t)Pcap, 256);
+  fl.phA = o;      o = align_up(o + 4 * (size_t)Pcap * V, 256);
+  fl.phC = o;      o = align_up(o + 4 * (size_t)Pcap * V, 256);
+  fl.phB = o;      o = align_up(o + 4 * (size_t)Pcap, 256);
+  fl.sig = o;      o = align_up(o + 8 * (size_t)Pcap, 256);
+  fl.blk = o;      o = align_up(o + 4 * (size_t)((P + kPrepTile - 1) / kPrepTile + 1), 256);
+  fl.meta = 0;     // lives in the batch header
+  fl.partial = o;
+  if (splits > 1) o = align_up(o + 8 * (size_t)splits * V * Ns * L, 256);
+  fl.total = o;
+  return fl;
+}
+
+rsim_status check_params(const rsim_radar_params* p, Consts* k) {
+  if (!p) return fail(RSIM_ERR_INVALID_ARG, "params is NULL");
+  if (p->M < 1 || p->N < 1 || p->Ns < 1 || p->L < 1)
+    return fail(RSIM_ERR_INVALID_ARG, "M, N, Ns and L must be >= 1");
+  if (!(p->lambda > 0) || !isfinite(p->lambda)) return fail(RSIM_ERR_INVALID_ARG, "lambda must be > 0");
+  if (!(p->fs > 0) || !isfinite(p->fs)) return fail(RSIM_ERR_INVALID_ARG, "fs must be > 0");
+  if (!isfinite(p->mu) || !isfinite(p->t_b) || !isfinite(p->t_slow) || !isfinite(p->d_rx) ||
+      !isfinite(p->c))
+    return fail(RSIM_ERR_INVALID_ARG, "radar parameters must be finite");
+  int64_t V, cells;
+  if (!mul_ok(p->M, p->N, &V) || V > (1 << 20)) return fail(RSIM_ERR_OVERFLOW, "M*N too large");
+  if (!mul_ok(V, p->Ns, &cells) || !mul_ok(cells, p->L, &cells) || cells > (int64_t(1) << 40))
+    return fail(RSIM_ERR_OVERFLOW, "M*N*Ns*L too large");
+  const double c = p->c > 0 ? p->c : 299792458.0;
+  const double d = p->d_rx > 0 ? p->d_rx : 0.5 * p->lambda;
+  const double ts = p->t_slow > 0 ? p->t_slow : p->M * p->t_b;
+  k->M = p->M;
+  k->N = p->N;
+  k->V = (int)V;
+  k->Ns = p->Ns;
+  k->L = p->L;
+  k->k_a0 = 2.0 * p->mu / (c * p->fs);
+  k->k_da = p->mu * d / (c * p->fs);
+  k->k_g = d / p->lambda;
+  k->k_b = -2.0 * ts / p->lambda;
+  return RSIM_OK;
+}
+
+rsim_status check_pixels(const rsim_pixels* px) {
+  if (!px) return fail(RSIM_ERR_INVALID_ARG, "pixels is NULL");
+  if (px->P < 0) return fail(RSIM_ERR_INVALID_ARG, "P must be >= 0");
+  if (px->P >= (int64_t(1) << 31) - 1024) return fail(RSIM_ERR_OVERFLOW, "P must be < 2^31");
+  if (px->dtype != RSIM_F32 && px->dtype != RSIM_F64)
+    return fail(RSIM_ERR_INVALID_ARG, "pixel dtype must be RSIM_F32 or RSIM_F64");
+  if (px->P > 0 && (!px->range || !px->sigma_re || !px->sigma_im || !px->az || !px->el || !px->vel))
+    return fail(RSIM_ERR_INVALID_ARG, "a pixel array pointer is NULL");
+  return RSIM_OK;
+}
+
+bool tier_ok(int tier) { return tier >= RSIM_TIER_FP32 && tier <= RSIM_TIER_FP16; }
+
+std::string plan_key(int tier, const Consts& k, int64_t P) {
+  char b[160];
+  snprintf(b, sizeof b, "t%d_V%d_Ns%d_L%d_P%lld", tier, k.V, k.Ns, k.L, (long long)P);
+  return b;
+}
+
+rsim_plan choose_plan(rsim_ctx* ctx, int tier, const Consts& k, int64_t P) {
+  {
+    std::lock_guard<std::mutex> g(ctx->plan_mu);
+    auto it = ctx->plans.find(plan_key(tier, k, P));
+    if (it != ctx->plans.end()) return it->second;
+  }
+  rsim_plan p{};
+  p.splits = default_splits(tier, k.V, k.Ns, k.L, P, ctx->num_sms);
+  p.chunk_px = kChunkPx;
+  p.grid = 0;
+  p.variant = 0;
+  p.tuned = 0;
+  return p;
+}
+
+// Workspace bytes for F frames of P_f pixels with the given splits.
+size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits) {
+  size_t o = align_up(sizeof(FrameIO) * (size_t)F, 256);  // frame table
+  o = align_up(o + 16 * (size_t)F, 256);                  // meta
+  o = align_up(o + 256, 256);                             // unit counter + spare
+  for (int f = 0; f < F; ++f) {
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], splits, o);
+    o = fl.total;
+  }
+  return o;
+}
+
+rsim_status ensure_workspace(rsim_ctx* ctx, size_t bytes, cudaStream_t st) {
+  if (ctx->ws_bytes >= bytes) return RSIM_OK;
+  if (ctx->budget && bytes > ctx->budget)
+    return fail(RSIM_ERR_BUDGET, "workspace of " + std::to_string(bytes) +
+                                     " bytes exceeds the context budget of " +
+                                     std::to_string(ctx->budget));
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  if (ctx->ws) cudaFree(ctx->ws);
+  ctx->ws = nullptr;
+  ctx->ws_bytes = 0;
+  size_t want = align_up(bytes + bytes / 8, 1 << 20);
+  if (ctx->budget && want > ctx->budget) want = bytes;
+  e = cudaMalloc(&ctx->ws, want);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(RSIM_ERR_OOM, "cudaMalloc of the workspace (" + std::to_string(want) + " bytes) failed");
+  }
+  ctx->ws_bytes = want;
+  return RSIM_OK;
+}
+
+// Fill FrameIO entries for F frames in workspace `ws` and upload the table.
+rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pixels* frames,
+                         int F, void* const* cubes, int splits, cudaStream_t st,
+                         std::vector<FrameIO>& host, FrameIO** dev_table, int** counter) {
+  host.assign(F, FrameIO{});
+  size_t o = align_up(sizeof(FrameIO) * (size_t)F, 256);
+  unsigned long long* meta = (unsigned long long*)(ws + o);
+  o = align_up(o + 16 * (size_t)F, 256);
+  *counter = (int*)(ws + o);
+  o = align_up(o + 256, 256);
+  for (int f = 0; f < F; ++f) {
+    const rsim_pixels& px = frames[f];
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, px.P, splits, o);
+    o = fl.total;
+    FrameIO& io = host[f];
+    io.range = px.range;
+    io.sre = px.sigma_re;
+    io.sim = px.sigma_im;
+    io.az = px.az;
+    io.el = px.el;
+    io.vel = px.vel;
+    io.cube = cubes ? cubes[f] : nullptr;
+    io.P = px.P;
+    io.Pcap = fl.Pcap;
+    io.idx = (int32_t*)(ws + fl.idx);
+    io.phA = (uint32_t*)(ws + fl.phA);
+    io.phC = (uint32_t*)(ws + fl.phC);
+    io.phB = (uint32_t*)(ws + fl.phB);
+    io.sig = (float2*)(ws + fl.sig);
+    io.blk_count = (int32_t*)(ws + fl.blk);
+    io.meta = meta + 2 * f;
+    io.partial = splits > 1 ? (float2*)(ws + fl.partial) : nullptr;
+    io.splits = splits;
+  }
+  *dev_table = (FrameIO*)ws;
+  cudaError_t e = cudaMemcpyAsync(ws, host.data(), sizeof(FrameIO) * (size_t)F,
+                                  cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
+  e = cudaMemsetAsync(meta, 0, 16 * (size_t)F, st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(meta)");
+  return RSIM_OK;
+}
+
+int64_t max_P(const rsim_pixels* frames, int F) {
+  int64_t m = 0;
+  for (int f = 0; f < F; ++f) m = std::max(m, frames[f].P);
+  return m;
+}
+
+// The stage sequence shared by rsim_synth, rsim_synth_batch and the server.
+rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k,
+                       const rsim_pixels* frames, int F, void* const* cubes, int tier,
+                       int out_dtype, const rsim_plan& plan, unsigned* status, cudaStream_t st) {
+  std::vector<int64_t> Ps(F);
+  for (int f = 0; f < F; ++f) Ps[f] = frames[f].P;
+  const int splits = plan.splits;
+  if (batch_bytes(k, Ps.data(), F, splits) > ws_bytes)
+    return fail(RSIM_ERR_INVALID_ARG, "workspace too small for this request");
+  std::vector<FrameIO> host;
+  FrameIO* table = nullptr;
+  int* counter = nullptr;
+  rsim_status s = stage_frames(ctx, ws, k, frames, F, cubes, splits, st, host, &table, &counter);
+  if (s != RSIM_OK) return s;
+  const int64_t mp = max_P(frames, F);
+  // stage events when profiling this context's own calls
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  const bool prof = ctx->prof && status == ctx->status_dev;
+  if (prof) {
+    const size_t base = 4 * (size_t)ctx->prof_calls;
+    while (ctx->ev_pool.size() < base + 4) {
+      cudaEvent_t x;
+      if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+      ctx->ev_pool.push_back(x);
+    }
+    for (int i = 0; i < 4; ++i) ev[i] = ctx->ev_pool[base + i];
+    ctx->prof_calls++;
+    ctx->prof_kernels += 3 + (splits > 1 ? 1 : 0);
+    cudaEventRecord(ev[0], st);
+  }
+  cudaError_t e = launch_prep(k, table, F, mp, frames[0].dtype, false, status, st);
+  if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
+  if (prof) cudaEventRecord(ev[1], st);
+  if (tier == RSIM_TIER_FP32) {
+    e = launch_direct(k, table, F, splits, out_dtype, st);
+    if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
+    if (prof) cudaEventRecord(ev[2], st);
+    if (splits > 1) {
+      e = launch_reduce(k, table, F, splits, out_dtype, 0.f, st);
+      if (e != cudaSuccess) return cuda_fail(e, "split reduction");
+    }
+  } else {
+    e = cudaMemsetAsync(counter, 0, 256, st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
+    e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, ctx->num_sms, status, counter,
+                    st);
+    if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
+    if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
+    if (prof) cudaEventRecord(ev[2], st);
+    if (splits > 1) {
+      const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
+      e = launch_reduce(k, table, F, splits, out_dtype, scaled ? 1.f : 0.f, st);
+      if (e != cudaSuccess) return cuda_fail(e, "split reduction");
+    }
+  }
+  if (prof) cudaEventRecord(ev[3], st);
+  return RSIM_OK;
+}
+
+}  // namespace rsim
+
+using namespace rsim;
+
+extern "C" {
+
+const char* rsim_version(void) { return "rsim 0.1 (sm_103a)"; }
+
+const char* rsim_last_error(void) { return g_last_error.c_str(); }
+
+rsim_status rsim_create(rsim_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return fail(RSIM_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= n) return fail(RSIM_ERR_INVALID_ARG, "no such device");
+  e = cudaSetDevice(device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+  rsim_ctx* c = new rsim_ctx();
+  c->device = device;
+  c->num_sms = prop.multiProcessorCount;
+  c->cc_major = prop.major;
+  c->cc_minor = prop.minor;
+  c->budget = hbm_budget_bytes;
+  e = cudaMalloc(&c->status_dev, 256);
+  if (e != cudaSuccess) {
+    delete c;
+    return cuda_fail(e, "cudaMalloc(status)");
+  }
+  cudaMemset(c->status_dev, 0, 256);
+  load_plan_cache(c);
+  *out = c;
+  return RSIM_OK;
+}
+
+rsim_status rsim_destroy(rsim_ctx* ctx) {
+  if (!ctx) return RSIM_OK;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->status_dev) cudaFree(ctx->status_dev);
+  for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  delete ctx;
+  return RSIM_OK;
+}
+
+rsim_status rsim_workspace_size(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
+                                rsim_tier tier, size_t* bytes) {
+  if (!ctx || !bytes) return fail(RSIM_ERR_INVALID_ARG, "ctx or bytes is NULL");
+  if (!tier_ok(tier)) return fail(RSIM_ERR_INVALID_ARG, "unknown tier");
+  if (P < 0) return fail(RSIM_ERR_INVALID_ARG, "P must be >= 0");
+  Consts k;
+  rsim_status s = check_params(params, &k);
+  if (s != RSIM_OK) return s;
+  rsim_plan plan = choose_plan(ctx, tier, k, P);
+  *bytes = batch_bytes(k, &P, 1, plan.splits);
+  return RSIM_OK;
+}
+
+rsim_status rsim_synth(rsim_ctx* ctx, const rsim_radar_params* params, const rsim_pixels* pixels,
+                       rsim_tier tier, void* cube, int32_t out_dtype, rsim_stream stream) {
+  void* cubes[1] = {cube};
+  return rsim_synth_batch(ctx, params, pixels, 1, cubes, tier, out_dtype, stream);
+}
+
+rsim_status rsim_synth_batch(rsim_ctx* ctx, const rsim_radar_params* params,
+                             const rsim_pixels* frames, int32_t F, void* const* cubes,
+                             rsim_tier tier, int32_t out_dtype, rsim_stream stream) {
+  if (!ctx) return fail(RSIM_ERR_INVALID_ARG, "ctx is NULL");
+  if (!frames || !cubes) return fail(RSIM_ERR_INVALID_ARG, "frames or cubes is NULL");
+  if (F < 1) return fail(RSIM_ERR_INVALID_ARG, "F must be >= 1");
+  if (!tier_ok(tier)) return fail(RSIM_ERR_INVALID_ARG, "unknown tier");
+  if (out_dtype != RSIM_C64 && out_dtype != RSIM_C128)
+    return fail(RSIM_ERR_INVALID_ARG, "out_dtype must be RSIM_C64 or RSIM_C128");
+  Consts k;
+  rsim_status s = check_params(params, &k);
+  if (s != RSIM_OK) return s;
+  int64_t maxp = 0;
+  for (int f = 0; f < F; ++f) {
+    s = check_pixels(&frames[f]);
+    if (s != RSIM_OK) return s;
+    if (!cubes[f]) return fail(RSIM_ERR_INVALID_ARG, "a cube pointer is NULL");
+    if (frames[f].dtype != frames[0].dtype)
+      return fail(RSIM_ERR_INVALID_ARG, "all frames of a batch must share the pixel dtype");
+    maxp = std::max(maxp, frames[f].P);
+  }
+  if (tier != RSIM_TIER_FP32 && !(ctx->cc_major == 10 && ctx->cc_minor == 3))
+    return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tiers need an sm_103 device");
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  // the plan of a batch is the plan of its largest frame: every frame uses the same
+  // splits rule, so a frame gives the same bits alone and in a batch of equal-P frames
+  rsim_plan plan = choose_plan(ctx, tier, k, maxp);
+  std::vector<int64_t> Ps(F);
+  for (int f = 0; f < F; ++f) Ps[f] = frames[f].P;
+  const size_t need = batch_bytes(k, Ps.data(), F, plan.splits);
+  s = ensure_workspace(ctx, need, st);
+  if (s != RSIM_OK) return s;
+  return run_frames(ctx, (char*)ctx->ws, ctx->ws_bytes, k, frames, F, cubes, tier, out_dtype, plan,
+                    ctx->status_dev, st);
+}
+
+rsim_status rsim_valid_indices(rsim_ctx* ctx, const rsim_pixels* pixels, int32_t* idx,
+                               int64_t* p_valid, rsim_stream stream) {
+  if (!ctx || !idx || !p_valid) return fail(RSIM_ERR_INVALID_ARG, "NULL argument");
+  rsim_status s = check_pixels(pixels);
+  if (s != RSIM_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(ctx->device);
+  Consts k{};
+  k.V = 1;
+  k.Ns = 1;
+  k.L = 1;
+  int64_t P = pixels->P;
+  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, 1), st);
+  if (s != RSIM_OK) return s;
+  std::vector<FrameIO> host;
+  FrameIO* table = nullptr;
+  int* counter = nullptr;
+  void* cubes[1] = {nullptr};
+  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, st, host, &table, &counter);
+  if (s != RSIM_OK) return s;
+  // the index list goes straight to the caller's buffer; the count is copied after
+  host[0].idx = idx;
+  cudaError_t e = cudaMemcpyAsync(table, host.data(), sizeof(FrameIO), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
+  e = launch_prep(k, table, 1, P, pixels->dtype, true, ctx->status_dev, st);
+  if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
+  e = cudaMemcpyAsync(p_valid, host[0].meta, 8, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy of the valid count");
+  return RSIM_OK;
+}
+
+rsim_status rsim_path_phases(rsim_ctx* ctx, const rsim_radar_params* params,
+                             const rsim_pixels* pixels, uint32_t* a, uint32_t* cph, uint32_t* b,
+                             float* sigma, int64_t* p_valid, rsim_stream stream) {
+  if (!ctx || !a || !cph || !b || !sigma || !p_valid) return fail(RSIM_ERR_INVALID_ARG, "NULL argument");
+  Consts k;
+  rsim_status s = check_params(params, &k);
+  if (s != RSIM_OK) return s;
+  s = check_pixels(pixels);
+  if (s != RSIM_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaSetDevice(ctx->device);
+  int64_t P = pixels->P;
+  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, 1), st);
+  if (s != RSIM_OK) return s;
+  std::vector<FrameIO> host;
+  FrameIO* table = nullptr;
+  int* counter = nullptr;
+  void* cubes[1] = {nullptr};
+  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, st, host, &table, &counter);
+  if (s != RSIM_OK) return s;
+  host[0].phA = a;
+  host[0].phC = cph;
+  host[0].phB = b;
+  host[0].sig = (float2*)sigma;
+  host[0].Pcap = P;
+  cudaError_t e = cudaMemcpyAsync(table, host.data(), sizeof(FrameIO), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
+  e = launch_prep(k, table, 1, P, pixels->dtype, false, ctx->status_dev, st);
+  if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
+  e = cudaMemcpyAsync(p_valid, host[0].meta, 8, cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy of the valid count");
+  return RSIM_OK;
+}
+
+rsim_status rsim_sync_status(rsim_ctx* ctx, rsim_stream stream) {
+  if (!ctx) return fail(RSIM_ERR_INVALID_ARG, "ctx is NULL");
+  cudaSetDevice(ctx->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  unsigned w = 0;
+  e = cudaMemcpy(&w, ctx->status_dev, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read of the status word");
+  if (w) cudaMemset(ctx->status_dev, 0, 4);
+  if (w & kStatusTimeout) return fail(RSIM_ERR_TIMEOUT, "a device-side wait ran out of time");
+  if (w & kStatusNonfinite)
+    return fail(RSIM_ERR_NONFINITE, "a valid pixel has a non-finite field or R <= 0");
+  return RSIM_OK;
+}
+
+rsim_status rsim_profile_enable(rsim_ctx* ctx, int32_t on) {
+  if (!ctx) return fail(RSIM_ERR_INVALID_ARG, "ctx is NULL");
+  ctx->prof = on != 0;
+  ctx->prof_calls = 0;
+  ctx->prof_kernels = 0;
+  return RSIM_OK;
+}
+
+rsim_status rsim_profile_read(rsim_ctx* ctx, rsim_profile* out) {
+  if (!ctx || !out) return fail(RSIM_ERR_INVALID_ARG, "NULL argument");
+  cudaSetDevice(ctx->device);
+  rsim_profile p{};
+  p.calls = ctx->prof_calls;
+  p.kernels = ctx->prof_kernels;
+  for (int c = 0; c < ctx->prof_calls; ++c) {
+    cudaEvent_t* ev = &ctx->ev_pool[4 * (size_t)c];
+    cudaError_t e = cudaEventSynchronize(ev[3]);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+    float a = 0, b = 0, d = 0;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    cudaEventElapsedTime(&d, ev[2], ev[3]);
+    p.prep_ms += a;
+    p.contract_ms += b;
+    p.reduce_ms += d;
+  }
+  ctx->prof_calls = 0;
+  ctx->prof_kernels = 0;
+  *out = p;
+  return RSIM_OK;
+}
+
+rsim_status rsim_get_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
+                          rsim_tier tier, rsim_plan* plan) {
+  if (!ctx || !plan) return fail(RSIM_ERR_INVALID_ARG, "NULL argument");
+  if (!tier_ok(tier)) return fail(RSIM_ERR_INVALID_ARG, "unknown tier");
+  Consts k;
+  rsim_status s = check_params(params, &k);
+  if (s != RSIM_OK) return s;
+  *plan = choose_plan(ctx, tier, k, P);
+  return RSIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Internal declarations shared by the CUDA sources of librsim (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rsim.h"
+
+namespace rsim {
+
+constexpr int kChunkPx = 32;        // pixels per pipeline stage / K-chunk (64 real K)
+constexpr int kPrepTile = 1024;     // pixels per block of the compaction kernels
+constexpr int kPrepThreads = 256;
+constexpr int kMaxSplits = 64;
+
+// Host-resolved constants of one radar configuration.  The per-pixel FP64 phase
+// increments are products of these with R, u and vel (Eq. 1 / Eq. 2):
+//   a_{p,v} = k_a0 R_p + v k_da u_p    (2 mu R_{p,v} / (c F_s), cycles per sample)
+//   c_{p,v} = v k_g u_p                (v d_rx u_p / lambda, cycles)
+//   b_p     = k_b vel_p                (-2 vel_p T_slow / lambda, cycles per block)
+struct Consts {
+  int M, N, V, Ns, L;
+  double k_a0, k_da, k_g, k_b;
+};
+
+// One frame as the kernels see it: caller buffers plus this frame's workspace slices.
+struct FrameIO {
+  const void* range;
+  const void* sre;
+  const void* sim;
+  const void* az;
+  const void* el;
+  const void* vel;
+  void* cube;                 // [V][Ns][L] complex (out_dtype)
+  int64_t P;                  // pixels in the frame
+  int64_t Pcap;               // row stride of phA / phC (>= P, multiple of 64)
+  int32_t* idx;               // [Pcap] ascending valid indices
+  uint32_t* phA;              // [V][Pcap] fast-time increment, 2^-32 cycle/sample
+  uint32_t* phC;              // [V][Pcap] spatial phase, 2^-32 cycle
+  uint32_t* phB;              // [Pcap]    slow-time increment, 2^-32 cycle/block
+  float2* sig;                // [Pcap]    sigma (FP32)
+  int32_t* blk_count;         // [ceil(P / kPrepTile)] valid pixels per prep block
+  unsigned long long* meta;   // [0] P_valid, [1] max(|re|,|im|) of sigma as float bits
+  float2* partial;            // [splits][V*Ns][L] split partial sums (NULL if splits == 1)
+  int32_t splits;             // pixel splits of the contraction
+  int32_t pad;
+};
+
+// Device status word bits (OR-ed by kernels, read by rsim_sync_status).
+enum : unsigned { kStatusNonfinite = 1u, kStatusTimeout = 2u };
+
+// Workspace slices of one frame, as byte offsets from a base pointer.
+struct FrameLayout {
+  size_t idx, phA, phC, phB, sig, blk, meta, partial, total;
+  int64_t Pcap;
+};
+FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, size_t base);
+
+// Launches (all asynchronous on `st`).  `frames` is a device array of F FrameIO.
+cudaError_t launch_prep(const Consts& k, const FrameIO* frames, int F, int64_t maxP, int dtype,
+                        bool write_idx_only, unsigned* status, cudaStream_t st);
+cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits,
+                          int out_dtype, cudaStream_t st);
+cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
+                          float scale_from_meta, cudaStream_t st);
+cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
+                        int out_dtype, int grid, int num_sms, unsigned* status, int* unit_counter,
+                        cudaStream_t st);
+
+// Plan rule shared by single-frame and batch paths (depends on the shape only).
+int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms);
+int units_per_split(int tier, int V, int Ns, int L);
+
+}  // namespace rsim
