@@ -204,6 +204,12 @@ typedef struct {
 rsim_status rsim_autotune(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
                           rsim_tier tier, rsim_plan* chosen, rsim_stream stream);
 
+/* Pin the plan for (params, P, tier) in the context's cache (replaces a tuned or default
+ * plan).  plan->splits in 1..64; plan->grid 0 (one CTA per SM) or a positive CTA count.
+ * Host only.  Errors: INVALID_ARG. */
+rsim_status rsim_set_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
+                          rsim_tier tier, const rsim_plan* plan);
+
 /* The plan rsim_synth would use now for (params, P, tier).  Host only. */
 rsim_status rsim_get_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
                           rsim_tier tier, rsim_plan* plan);

@@ -90,6 +90,8 @@ SIGNATURES = {
                               POINTER(rsim_plan), c_void_p]),
     "rsim_profile_enable": (c_int, [c_void_p, c_int32]),
     "rsim_profile_read": (c_int, [c_void_p, POINTER(rsim_profile)]),
+    "rsim_set_plan": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
+                              POINTER(rsim_plan)]),
     "rsim_get_plan": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
                               POINTER(rsim_plan)]),
     "rsim_server_create": (c_int, [c_void_p, POINTER(rsim_server_opts), POINTER(c_void_p)]),
@@ -242,6 +244,12 @@ def rsim_profile_read(ctx) -> rsim_profile:
     p = rsim_profile()
     check(load().rsim_profile_read(ctx, ctypes.byref(p)))
     return p
+
+
+def rsim_set_plan(ctx, radar, P: int, tier: int, splits: int, grid: int = 0, variant: int = 0):
+    plan = rsim_plan(int(splits), 32, int(grid), int(variant), 1)
+    check(load().rsim_set_plan(ctx, ctypes.byref(radar_params(radar)), int(P), int(tier),
+                               ctypes.byref(plan)))
 
 
 def rsim_get_plan(ctx, radar, P: int, tier: int) -> rsim_plan:

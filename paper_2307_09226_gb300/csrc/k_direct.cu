@@ -189,6 +189,17 @@ cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int spl
   return cudaGetLastError();
 }
 
+bool uses_partial(int tier, int64_t P, int splits) {
+  if (splits > 1) return true;
+  if (tier == RSIM_TIER_FP32) return false;
+  const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
+  return chunks > group_chunks(tier);
+}
+
+int group_chunks(int tier) {
+  return (tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16) ? 32 : 96;
+}
+
 int units_per_split(int tier, int V, int Ns, int L) {
   if (tier == RSIM_TIER_FP32) return V * ((Ns + kTN - 1) / kTN) * ((L + kTL - 1) / kTL);
   const int64_t rows = (int64_t)V * Ns;
@@ -199,19 +210,35 @@ int units_per_split(int tier, int V, int Ns, int L) {
 int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms) {
   const int tiles = units_per_split(tier, V, Ns, L);
   const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
-  // FP32: about 4 resident CTAs per SM; tensor tiers: one persistent CTA per SM.
-  const int64_t target = (tier == RSIM_TIER_FP32) ? 4ll * num_sms : (int64_t)num_sms;
-  int64_t s = (target + tiles - 1) / tiles;
   // keep at least 8 chunks (256 pixels) per split
-  const int64_t smax = chunks / 8 > 0 ? chunks / 8 : 1;
-  if (s > smax) s = smax;
-  // FP32 accumulation: at most 8192 pixels per split, so that the running sum of
-  // random-phase terms keeps a relative rounding error of a few 1e-6 (the splits are
-  // then added in FP64)
-  if (tier == RSIM_TIER_FP32) s = std::max<int64_t>(s, (P + 8191) / 8192);
-  if (s > kMaxSplits) s = kMaxSplits;
-  if (s < 1) s = 1;
-  return (int)s;
+  int64_t smax = chunks / 8 > 0 ? chunks / 8 : 1;
+  if (smax > kMaxSplits) smax = kMaxSplits;
+  if (tier == RSIM_TIER_FP32) {
+    // about 4 resident CTAs per SM
+    int64_t s = (4ll * num_sms + tiles - 1) / tiles;
+    if (s > smax) s = smax;
+    // FP32 accumulation: at most 8192 pixels per split, so that the running sum of
+    // random-phase terms keeps a relative rounding error of a few 1e-6 (the splits are
+    // then added in FP64)
+    s = std::max<int64_t>(s, (P + 8191) / 8192);
+    if (s > kMaxSplits) s = kMaxSplits;
+    return (int)std::max<int64_t>(s, 1);
+  }
+  // tensor tiers: one persistent CTA per SM takes equal units from a counter; pick the
+  // split count whose unit count fills whole rounds of SMs best, with a small cost per
+  // split for the partial buffer it adds
+  double best = -1.0;
+  int bs = 1;
+  for (int s = 1; s <= smax; ++s) {
+    const int64_t units = (int64_t)tiles * s;
+    const int64_t rounds = (units + num_sms - 1) / num_sms;
+    const double eff = (double)units / (double)(rounds * num_sms) - 0.003 * s;
+    if (eff > best + 1e-9) {
+      best = eff;
+      bs = s;
+    }
+  }
+  return bs;
 }
 
 }  // namespace rsim

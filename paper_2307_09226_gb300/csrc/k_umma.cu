@@ -31,8 +31,11 @@
 namespace rsim {
 namespace {
 
-constexpr int kStages = 3;
-constexpr int kThreads = 288;              // 9 warps
+constexpr int kStages = 3;                 // operand stages (A in TMEM, B in smem)
+constexpr int kPixStages = 6;              // ring of staged per-chunk pixel phases
+constexpr int kUnitSlots = 4;              // ring of work-unit ids
+constexpr int kMaxCh = 8;                  // channels a row tile may span for staging
+constexpr int kThreads = 320;              // 10 warps
 constexpr int kBRowsMax = 256;             // N = 2 * NT <= 256
 constexpr int kBBytes = kBRowsMax * 128;   // one 16-bit operand part of one stage
 constexpr int kStageBytes = 2 * kBBytes;   // hi + lo
@@ -40,13 +43,26 @@ constexpr int kAccCols = 256;              // accumulator columns (N <= 256 FP32
 constexpr int kTmemCols = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait, then give up
 
+// Per-chunk pixel data staged by the loader warp (bulk copies from global memory).
+struct PixStage {
+  uint32_t a[kMaxCh][kChunkPx];  // fast-time increments of the tile's channels
+  uint32_t c[kMaxCh][kChunkPx];  // spatial phases of the tile's channels
+  uint32_t b[kChunkPx];          // slow-time increments
+  float2 s[kChunkPx];            // sigma
+};
+
 struct Shared {
   uint64_t a_full[kStages];
   uint64_t b_full[kStages];
   uint64_t empty[kStages];
+  uint64_t pix_full[kPixStages];
+  uint64_t pix_empty[kPixStages];
+  uint64_t unit_full[kUnitSlots];
+  uint64_t unit_empty[kUnitSlots];
   uint64_t acc_full;
   uint64_t acc_empty;
   uint64_t fin;
+  long long unit[kUnitSlots];
   uint32_t tmem_base;
   int abort;
 };
@@ -98,6 +114,23 @@ __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, Shared* sh,
       }
     }
   }
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                   smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+
+// 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16) that
+// completes `bytes` of the barrier's transaction count.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
 }
 
 __device__ __forceinline__ void fence_before() {
@@ -189,18 +222,21 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t&
 }
 
 struct Geo {
-  int mtiles, ntiles, NT, splits, upf;
+  int mtiles, ntiles, NT, splits, upf, group, direct, F;
   int64_t total_units;
+  const int32_t* order;  // frames by decreasing valid-pixel count
 };
 
 struct Unit {
   int f, mt, nt, s;
   int64_t c0, c1, pv;
+  int v_first, span;
 };
 
-__device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, int64_t u) {
+__device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, const Consts& k,
+                                       int64_t u) {
   Unit x;
-  x.f = (int)(u / g.upf);
+  x.f = g.order[u / g.upf];
   int r = (int)(u % g.upf);
   x.s = r % g.splits;
   r /= g.splits;
@@ -210,6 +246,11 @@ __device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, int6
   const int64_t nch = (x.pv + kChunkPx - 1) / kChunkPx;
   x.c0 = nch * x.s / g.splits;
   x.c1 = nch * (x.s + 1) / g.splits;
+  const int64_t rows = (int64_t)k.V * k.Ns;
+  const int64_t r0 = (int64_t)x.mt * 128;
+  const int64_t r1 = (r0 + 127 < rows ? r0 + 127 : rows - 1);
+  x.v_first = (int)(r0 / k.Ns);
+  x.span = (int)(r1 / k.Ns) - x.v_first + 1;
   return x;
 }
 
@@ -220,14 +261,37 @@ __device__ __forceinline__ float sigma_scale(const FrameIO& fr, int scaled) {
   return m > 0.f ? ldexpf(1.f, -(ilogbf(m) + 1)) : 1.f;
 }
 
+// Warp-collective wait: all lanes poll, the decision is made uniform.
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, Shared* sh, unsigned* status) {
+  return __all_sync(0xffffffffu, mbar_wait(b, parity, sh, status));
+}
+
+// Next work unit id from the ring filled by the loader (-1: no more work).
+__device__ __forceinline__ bool next_unit(Shared* sh, uint32_t ui, unsigned* status, long long* u,
+                                          bool warp_collective) {
+  const uint32_t slot = ui % kUnitSlots, ph = (ui / kUnitSlots) & 1u;
+  const bool ok = warp_collective ? warp_wait(&sh->unit_full[slot], ph, sh, status)
+                                  : mbar_wait(&sh->unit_full[slot], ph, sh, status);
+  if (!ok) return false;
+  *u = *(volatile long long*)&sh->unit[slot];
+  if (warp_collective) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&sh->unit_empty[slot]);
+  } else {
+    mbar_arrive(&sh->unit_empty[slot]);
+  }
+  return *u >= 0;
+}
+
 template <int BF, int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, int out_dtype,
-              unsigned* status) {
+              unsigned* status, int* unit_counter) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* bstage = smem;  // kStages x (hi, lo) x 32 KB
-  Shared* sh = (Shared*)(smem + kStages * kStageBytes);
+  unsigned char* bstage = smem;  // kStages x (hi, lo) x 32 KB, 1024-aligned
+  PixStage* pix = (PixStage*)(smem + kStages * kStageBytes);
+  Shared* sh = (Shared*)(pix + kPixStages);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = 2 * g.NT;
@@ -238,6 +302,14 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
       mbar_init(&sh->a_full[i], 128);
       mbar_init(&sh->b_full[i], 128);
       mbar_init(&sh->empty[i], 1);
+    }
+    for (int i = 0; i < kPixStages; ++i) {
+      mbar_init(&sh->pix_full[i], 1);
+      mbar_init(&sh->pix_empty[i], 8);  // 4 A warps + 4 B warps
+    }
+    for (int i = 0; i < kUnitSlots; ++i) {
+      mbar_init(&sh->unit_full[i], 1);
+      mbar_init(&sh->unit_empty[i], 9);  // 4 A warps + 4 B warps + the MMA thread
     }
     mbar_init(&sh->acc_full, 1);
     mbar_init(&sh->acc_empty, 128);
@@ -259,100 +331,129 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   const int64_t rows_total = (int64_t)k.V * k.Ns;
 
   if (warp < 4) {
-    // ---------------- A producers + epilogue: thread = accumulator row ----------------
+    // ------------- A producers + accumulator drain: thread = accumulator row -------------
     const int r = warp * 32 + lane;
     const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
-    uint32_t kk = 0;  // stage counter across units
-    uint32_t ui = 0;  // unit counter
-    for (int64_t u = blockIdx.x; u < g.total_units; u += gridDim.x, ++ui) {
-      const Unit x = decode(g, frames, u);
+    uint32_t kk = 0, pk = 0, gi = 0, ui = 0;
+    long long u;
+    bool alive = true;
+    while (alive && next_unit(sh, ui++, status, &u, true)) {
+      const Unit x = decode(g, frames, k, u);
       const FrameIO& fr = frames[x.f];
       const int64_t gr = (int64_t)x.mt * 128 + r;
       const bool row_ok = gr < rows_total;
-      const int v = row_ok ? (int)(gr / k.Ns) : 0;
+      const int v = row_ok ? (int)(gr / k.Ns) : x.v_first;
       const uint32_t n = row_ok ? (uint32_t)(gr % k.Ns) : 0u;
+      const bool staged = x.span <= kMaxCh;
+      const int vl = v - x.v_first;
       const uint32_t* pA = fr.phA + (int64_t)v * fr.Pcap;
       const uint32_t* pC = fr.phC + (int64_t)v * fr.Pcap;
-      bool alive = true;
-      for (int64_t c = x.c0; c < x.c1 && alive; ++c, ++kk) {
-        const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-        // warp-uniform decision: the tensor-memory stores below are warp-collective
-        if (!__all_sync(0xffffffffu, mbar_wait(&sh->empty[st], ph ^ 1u, sh, status))) {
+      const float oscale = 1.f / sigma_scale(fr, scaled);
+      const int l0 = x.nt * g.NT;
+      int64_t g0 = x.c0;
+      do {
+        const int64_t g1 = (x.c1 < g0 + g.group) ? x.c1 : g0 + g.group;
+        for (int64_t c = g0; c < g1; ++c, ++kk, ++pk) {
+          const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
+          const uint32_t ps = pk % kPixStages, pph = (pk / kPixStages) & 1u;
+          if (!warp_wait(&sh->empty[st], ph ^ 1u, sh, status) ||
+              !warp_wait(&sh->pix_full[ps], pph, sh, status)) {
+            alive = false;
+            break;
+          }
+          uint32_t hi[32], lo[32];
+          const int64_t q0 = c * kChunkPx;
+#pragma unroll
+          for (int j4 = 0; j4 < kChunkPx; j4 += 4) {
+            uint4 a4, c4;
+            if (staged) {
+              a4 = *reinterpret_cast<const uint4*>(&pix[ps].a[vl][j4]);
+              c4 = *reinterpret_cast<const uint4*>(&pix[ps].c[vl][j4]);
+            } else {
+              a4 = *reinterpret_cast<const uint4*>(pA + q0 + j4);
+              c4 = *reinterpret_cast<const uint4*>(pC + q0 + j4);
+            }
+            const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
+            const uint32_t cv[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              float2 f = cis_q32(av[t] * n + cv[t]);
+              if (!row_ok || q0 + j4 + t >= x.pv) f = make_float2(0.f, 0.f);
+              split2<BF>(f.x, f.y, hi[j4 + t], lo[j4 + t]);
+            }
+          }
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&sh->pix_empty[ps]);
+          const uint32_t col = tmem + lane_base + kAccCols + st * 64;
+          tmem_st32(col, hi);
+          if (SPLIT) tmem_st32(col + 32, lo);
+          asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+          fence_before();
+          mbar_arrive(&sh->a_full[st]);
+        }
+        if (!alive) break;
+        // ---- drain this group's accumulator (round-to-nearest FP32 adds) ----
+        if (!warp_wait(&sh->acc_full, gi & 1u, sh, status)) {
           alive = false;
           break;
         }
-        uint32_t hi[32], lo[32];
-        const int64_t q0 = c * kChunkPx;
-#pragma unroll
-        for (int j4 = 0; j4 < kChunkPx; j4 += 4) {
-          const uint4 a4 = *reinterpret_cast<const uint4*>(pA + q0 + j4);
-          const uint4 c4 = *reinterpret_cast<const uint4*>(pC + q0 + j4);
-          const uint32_t av[4] = {a4.x, a4.y, a4.z, a4.w};
-          const uint32_t cv[4] = {c4.x, c4.y, c4.z, c4.w};
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            float2 f = cis_q32(av[t] * n + cv[t]);
-            if (!row_ok || q0 + j4 + t >= x.pv) f = make_float2(0.f, 0.f);
-            split2<BF>(f.x, f.y, hi[j4 + t], lo[j4 + t]);
-          }
-        }
-        const uint32_t col = tmem + lane_base + kAccCols + st * 64;
-        tmem_st32(col, hi);
-        if (SPLIT) tmem_st32(col + 32, lo);
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        fence_before();
-        mbar_arrive(&sh->a_full[st]);
-      }
-      if (!alive) break;
-      // ---- epilogue: accumulator rows -> partial sums (or the cube) ----
-      if (!__all_sync(0xffffffffu, mbar_wait(&sh->acc_full, ui & 1u, sh, status))) break;
-      fence_after();
-      const bool empty_unit = (x.c1 <= x.c0);
-      const float oscale = 1.f / sigma_scale(fr, scaled);
-      const int l0 = x.nt * g.NT;
-      for (int j0 = 0; j0 < g.NT; j0 += 8) {
-        uint32_t re[8], im[8];
-        if (!empty_unit) {
-          tmem_ld8(tmem + lane_base + j0, re);
-          tmem_ld8(tmem + lane_base + g.NT + j0, im);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        } else {
-#pragma unroll
-          for (int i = 0; i < 8; ++i) re[i] = im[i] = 0u;
-        }
-        if (!row_ok) continue;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int l = l0 + j0 + i;
-          if (l >= k.L) break;
-          const int64_t o = gr * k.L + l;
-          const float a = __uint_as_float(re[i]), b = __uint_as_float(im[i]);
-          if (g.splits == 1) {
-            if (out_dtype == RSIM_C128)
-              reinterpret_cast<double2*>(fr.cube)[o] = make_double2((double)a * oscale, (double)b * oscale);
-            else
-              reinterpret_cast<float2*>(fr.cube)[o] = make_float2(a * oscale, b * oscale);
+        fence_after();
+        const bool none = (g1 <= g0), first = (g0 == x.c0);
+        for (int j0 = 0; j0 < g.NT; j0 += 8) {
+          uint32_t re[8], im[8];
+          if (!none) {
+            tmem_ld8(tmem + lane_base + j0, re);
+            tmem_ld8(tmem + lane_base + g.NT + j0, im);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           } else {
-            fr.partial[(int64_t)x.s * rows_total * k.L + o] = make_float2(a, b);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) re[i] = im[i] = 0u;
+          }
+          if (!row_ok) continue;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const int l = l0 + j0 + i;
+            if (l >= k.L) break;
+            const int64_t o = gr * k.L + l;
+            const float a = __uint_as_float(re[i]), b = __uint_as_float(im[i]);
+            if (g.direct) {
+              if (out_dtype == RSIM_C128)
+                reinterpret_cast<double2*>(fr.cube)[o] = make_double2((double)a * oscale, (double)b * oscale);
+              else
+                reinterpret_cast<float2*>(fr.cube)[o] = make_float2(a * oscale, b * oscale);
+            } else {
+              float2* dst = fr.partial + (int64_t)x.s * rows_total * k.L + o;
+              if (first) {
+                *dst = make_float2(a, b);
+              } else {
+                const float2 p = *dst;
+                *dst = make_float2(p.x + a, p.y + b);
+              }
+            }
           }
         }
-      }
-      fence_before();
-      mbar_arrive(&sh->acc_empty);
+        fence_before();
+        mbar_arrive(&sh->acc_empty);
+        ++gi;
+        g0 = g1;
+      } while (g0 < x.c1);
     }
   } else if (warp < 8) {
-    // ---------------- B producers: the slow-time operand of this column tile ----------------
+    // ------------- B producers: sigma x slow-time phasors, real-embedded -------------
     const int t = threadIdx.x - 128;
-    uint32_t kk = 0;
-    for (int64_t u = blockIdx.x; u < g.total_units; u += gridDim.x) {
-      const Unit x = decode(g, frames, u);
+    uint32_t kk = 0, pk = 0, ui = 0;
+    long long u;
+    bool alive = true;
+    while (alive && next_unit(sh, ui++, status, &u, true)) {
+      const Unit x = decode(g, frames, k, u);
       const FrameIO& fr = frames[x.f];
       const float sc = sigma_scale(fr, scaled);
       const int l0 = x.nt * g.NT;
-      bool alive = true;
-      for (int64_t c = x.c0; c < x.c1; ++c, ++kk) {
+      for (int64_t c = x.c0; c < x.c1; ++c, ++kk, ++pk) {
         const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-        if (!mbar_wait(&sh->empty[st], ph ^ 1u, sh, status)) {
+        const uint32_t ps = pk % kPixStages, pph = (pk / kPixStages) & 1u;
+        if (!mbar_wait(&sh->empty[st], ph ^ 1u, sh, status) ||
+            !mbar_wait(&sh->pix_full[ps], pph, sh, status)) {
           alive = false;
           break;
         }
@@ -362,9 +463,9 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         for (int e = t; e < g.NT * 8; e += 128) {
           const int lt = e % g.NT, qg = e / g.NT;
           const int l = l0 + lt;
-          const uint4 b4 = *reinterpret_cast<const uint4*>(fr.phB + q0 + qg * 4);
-          const float4 s01 = *reinterpret_cast<const float4*>(fr.sig + q0 + qg * 4);
-          const float4 s23 = *reinterpret_cast<const float4*>(fr.sig + q0 + qg * 4 + 2);
+          const uint4 b4 = *reinterpret_cast<const uint4*>(&pix[ps].b[qg * 4]);
+          const float4 s01 = *reinterpret_cast<const float4*>(&pix[ps].s[qg * 4]);
+          const float4 s23 = *reinterpret_cast<const float4*>(&pix[ps].s[qg * 4 + 2]);
           const uint32_t bv[4] = {b4.x, b4.y, b4.z, b4.w};
           const float sr[4] = {s01.x, s01.z, s23.x, s23.z};
           const float si[4] = {s01.y, s01.w, s23.y, s23.w};
@@ -378,13 +479,8 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
               dre = a * w.x - b * w.y;
               dim = a * w.y + b * w.x;
             }
-            uint32_t h0, l0p, h1, l1p;
-            split2<BF>(dre, -dim, h0, l0p);  // row l      : (Re D, -Im D)
-            split2<BF>(dim, dre, h1, l1p);   // row NT + l : (Im D,  Re D)
-            rh[i] = h0;
-            rl[i] = l0p;
-            ih[i] = h1;
-            il[i] = l1p;
+            split2<BF>(dre, -dim, rh[i], rl[i]);  // row l      : (Re D, -Im D)
+            split2<BF>(dim, dre, ih[i], il[i]);   // row NT + l : (Im D,  Re D)
           }
           const int rre = lt, rim = g.NT + lt;
           const uint32_t ore = rre * 128 + (((uint32_t)qg ^ (rre & 7)) << 4);
@@ -396,50 +492,100 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
             *reinterpret_cast<uint4*>(blo + oim) = make_uint4(il[0], il[1], il[2], il[3]);
           }
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&sh->pix_empty[ps]);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_arrive(&sh->b_full[st]);
       }
-      if (!alive) break;
     }
-  } else if (warp == 8 && lane == 0) {
-    // ---------------- MMA issuer ----------------
-    uint32_t kk = 0, ui = 0;
-    bool alive = true;
-    for (int64_t u = blockIdx.x; u < g.total_units && alive; u += gridDim.x, ++ui) {
-      const Unit x = decode(g, frames, u);
-      if (!mbar_wait(&sh->acc_empty, (ui & 1u) ^ 1u, sh, status)) break;
-      fence_after();
-      const uint32_t d_tmem = tmem;
-      uint32_t accum = 0;
-      for (int64_t c = x.c0; c < x.c1; ++c, ++kk) {
-        const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-        if (!mbar_wait(&sh->a_full[st], ph, sh, status) || !mbar_wait(&sh->b_full[st], ph, sh, status)) {
-          alive = false;
-          break;
-        }
-        fence_after();
-        const uint32_t a_hi = tmem + kAccCols + st * 64, a_lo = a_hi + 32;
-        const uint32_t b_hi = smem_u32(bstage + st * kStageBytes), b_lo = b_hi + kBBytes;
+  } else if (warp == 8) {
+    // ------------- MMA issuer (one thread) -------------
+    if (lane == 0) {
+      uint32_t kk = 0, gi = 0, ui = 0;
+      long long u;
+      bool alive = true;
+      while (alive && next_unit(sh, ui++, status, &u, false)) {
+        const Unit x = decode(g, frames, k, u);
+        int64_t g0 = x.c0;
+        do {
+          const int64_t g1 = (x.c1 < g0 + g.group) ? x.c1 : g0 + g.group;
+          if (!mbar_wait(&sh->acc_empty, (gi & 1u) ^ 1u, sh, status)) {
+            alive = false;
+            break;
+          }
+          fence_after();
+          uint32_t accum = 0;
+          for (int64_t c = g0; c < g1; ++c, ++kk) {
+            const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
+            if (!mbar_wait(&sh->a_full[st], ph, sh, status) || !mbar_wait(&sh->b_full[st], ph, sh, status)) {
+              alive = false;
+              break;
+            }
+            fence_after();
+            const uint32_t a_hi = tmem + kAccCols + st * 64, a_lo = a_hi + 32;
+            const uint32_t b_hi = smem_u32(bstage + st * kStageBytes), b_lo = b_hi + kBBytes;
 #pragma unroll
-        for (int ks = 0; ks < 4; ++ks) {
-          mma_ts(d_tmem, a_hi + ks * 8, sdesc_sw128(b_hi + ks * 32), idesc, accum);
-          accum = 1;
-          if (SPLIT) {
-            mma_ts(d_tmem, a_hi + ks * 8, sdesc_sw128(b_lo + ks * 32), idesc, 1);
-            mma_ts(d_tmem, a_lo + ks * 8, sdesc_sw128(b_hi + ks * 32), idesc, 1);
+            for (int ks = 0; ks < 4; ++ks) {
+              mma_ts(tmem, a_hi + ks * 8, sdesc_sw128(b_hi + ks * 32), idesc, accum);
+              accum = 1;
+              if (SPLIT) {
+                mma_ts(tmem, a_hi + ks * 8, sdesc_sw128(b_lo + ks * 32), idesc, 1);
+                mma_ts(tmem, a_lo + ks * 8, sdesc_sw128(b_hi + ks * 32), idesc, 1);
+              }
+            }
+            mma_commit(&sh->empty[st]);
+          }
+          if (!alive) break;
+          if (g1 > g0)
+            mma_commit(&sh->acc_full);
+          else
+            mbar_arrive(&sh->acc_full);
+          ++gi;
+          g0 = g1;
+        } while (g0 < x.c1);
+      }
+      // every issued MMA completes before tensor memory is released
+      mma_commit(&sh->fin);
+      mbar_wait(&sh->fin, 0, sh, status);
+    }
+  } else {
+    // ------------- loader: work units + bulk copies of per-chunk pixel phases -------------
+    if (lane == 0) {
+      uint32_t pk = 0;
+      for (uint32_t ui = 0;; ++ui) {
+        const long long uu = (long long)atomicAdd(unit_counter, 1);
+        const long long u = uu < g.total_units ? uu : -1;
+        const uint32_t slot = ui % kUnitSlots, uph = (ui / kUnitSlots) & 1u;
+        if (!mbar_wait(&sh->unit_empty[slot], uph ^ 1u, sh, status)) break;
+        *(volatile long long*)&sh->unit[slot] = u;
+        mbar_arrive(&sh->unit_full[slot]);
+        if (u < 0) break;
+        const Unit x = decode(g, frames, k, u);
+        const FrameIO& fr = frames[x.f];
+        const bool staged = x.span <= kMaxCh;
+        bool alive = true;
+        for (int64_t c = x.c0; c < x.c1; ++c, ++pk) {
+          const uint32_t ps = pk % kPixStages, pph = (pk / kPixStages) & 1u;
+          if (!mbar_wait(&sh->pix_empty[ps], pph ^ 1u, sh, status)) {
+            alive = false;
+            break;
+          }
+          const int64_t q0 = c * kChunkPx;
+          const uint32_t bytes = 4 * kChunkPx + 8 * kChunkPx + (staged ? 8u * kChunkPx * x.span : 0u);
+          mbar_expect_tx(&sh->pix_full[ps], bytes);
+          bulk_g2s(pix[ps].b, fr.phB + q0, 4 * kChunkPx, &sh->pix_full[ps]);
+          bulk_g2s(pix[ps].s, fr.sig + q0, 8 * kChunkPx, &sh->pix_full[ps]);
+          if (staged) {
+            for (int i = 0; i < x.span; ++i) {
+              const int64_t ro = (int64_t)(x.v_first + i) * fr.Pcap + q0;
+              bulk_g2s(pix[ps].a[i], fr.phA + ro, 4 * kChunkPx, &sh->pix_full[ps]);
+              bulk_g2s(pix[ps].c[i], fr.phC + ro, 4 * kChunkPx, &sh->pix_full[ps]);
+            }
           }
         }
-        mma_commit(&sh->empty[st]);
+        if (!alive) break;
       }
-      if (!alive) break;
-      if (x.c1 > x.c0)
-        mma_commit(&sh->acc_full);
-      else
-        mbar_arrive(&sh->acc_full);
     }
-    // all issued MMAs complete before tensor memory is released
-    mma_commit(&sh->fin);
-    mbar_wait(&sh->fin, 0, sh, status);
   }
 
   fence_before();
@@ -451,22 +597,36 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   }
 }
 
+// Frames by decreasing valid-pixel count (ties by index): the persistent kernel takes
+// the units of the largest frames first.
+__global__ void order_frames(const FrameIO* __restrict__ frames, int F, int32_t* order) {
+  for (int f = threadIdx.x; f < F; f += blockDim.x) {
+    const unsigned long long pf = frames[f].meta[0];
+    int rank = 0;
+    for (int h = 0; h < F; ++h) {
+      const unsigned long long ph = frames[h].meta[0];
+      rank += (ph > pf) || (ph == pf && h < f);
+    }
+    order[rank] = f;
+  }
+}
+
 template <int BF, int SPLIT>
 cudaError_t launch_t(const Consts& k, const FrameIO* frames, const Geo& g, int grid, int scaled,
-                     int out_dtype, unsigned* status, cudaStream_t st) {
-  const int smem = kStages * kStageBytes + (int)sizeof(Shared) + 1024;
+                     int out_dtype, unsigned* status, int* counter, cudaStream_t st) {
+  const int smem = kStages * kStageBytes + kPixStages * (int)sizeof(PixStage) + (int)sizeof(Shared) + 1024;
   auto fn = umma_contract<BF, SPLIT>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, kThreads, smem, st>>>(frames, k, g, scaled, out_dtype, status);
+  fn<<<grid, kThreads, smem, st>>>(frames, k, g, scaled, out_dtype, status, counter);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
-                        int out_dtype, int grid, int num_sms, unsigned* status, int* /*unit_counter*/,
-                        cudaStream_t st) {
+                        int out_dtype, int grid, bool use_partial, int num_sms, unsigned* status,
+                        int* unit_counter, cudaStream_t st) {
   Geo g;
   const int64_t rows = (int64_t)k.V * k.Ns;
   g.NT = k.L >= 128 ? 128 : ((k.L + 7) / 8) * 8;
@@ -474,19 +634,28 @@ cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int split
   g.mtiles = (int)((rows + 127) / 128);
   g.splits = splits;
   g.upf = g.mtiles * g.ntiles * splits;
+  g.group = group_chunks(tier);
+  g.direct = use_partial ? 0 : 1;
+  g.F = F;
   g.total_units = (int64_t)g.upf * F;
   if (g.total_units <= 0) return cudaSuccess;
+  // the unit counter (int) and the frame order (F ints) share the counter region
+  int32_t* order = unit_counter + 4;
+  g.order = order;
+  order_frames<<<1, 256, 0, st>>>(frames, F, order);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   int blocks = grid > 0 ? grid : num_sms;
   if (blocks > g.total_units) blocks = (int)g.total_units;
   switch (tier) {
     case RSIM_TIER_BF16:
-      return launch_t<1, 0>(k, frames, g, blocks, 0, out_dtype, status, st);
+      return launch_t<1, 0>(k, frames, g, blocks, 0, out_dtype, status, unit_counter, st);
     case RSIM_TIER_SPLIT_BF16:
-      return launch_t<1, 1>(k, frames, g, blocks, 0, out_dtype, status, st);
+      return launch_t<1, 1>(k, frames, g, blocks, 0, out_dtype, status, unit_counter, st);
     case RSIM_TIER_SPLIT_FP16:
-      return launch_t<0, 1>(k, frames, g, blocks, 1, out_dtype, status, st);
+      return launch_t<0, 1>(k, frames, g, blocks, 1, out_dtype, status, unit_counter, st);
     case RSIM_TIER_FP16:
-      return launch_t<0, 0>(k, frames, g, blocks, 1, out_dtype, status, st);
+      return launch_t<0, 0>(k, frames, g, blocks, 1, out_dtype, status, unit_counter, st);
     default:
       return cudaErrorInvalidValue;
   }

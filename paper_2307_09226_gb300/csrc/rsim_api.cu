@@ -39,7 +39,7 @@ static bool mul_ok(int64_t a, int64_t b, int64_t* out) {
   return true;
 }
 
-FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, size_t base) {
+FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_partial, size_t base) {
   FrameLayout fl{};
   const int64_t Pcap = std::max<int64_t>(64, (P + 63) / 64 * 64);
   fl.Pcap = Pcap;
@@ -52,7 +52,7 @@ FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, size_t bas
   fl.blk = o;      o = align_up(o + 4 * (size_t)((P + kPrepTile - 1) / kPrepTile + 1), 256);
   fl.meta = 0;     // lives in the batch header
   fl.partial = o;
-  if (splits > 1) o = align_up(o + 8 * (size_t)splits * V * Ns * L, 256);
+  if (use_partial) o = align_up(o + 8 * (size_t)splits * V * Ns * L, 256);
   fl.total = o;
   return fl;
 }
@@ -120,12 +120,15 @@ rsim_plan choose_plan(rsim_ctx* ctx, int tier, const Consts& k, int64_t P) {
 }
 
 // Workspace bytes for F frames of P_f pixels with the given splits.
-size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits) {
+size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits, int tier) {
+  int64_t mp = 0;
+  for (int f = 0; f < F; ++f) mp = std::max(mp, P[f]);
+  const bool up = uses_partial(tier, mp, splits);
   size_t o = align_up(sizeof(FrameIO) * (size_t)F, 256);  // frame table
   o = align_up(o + 16 * (size_t)F, 256);                  // meta
-  o = align_up(o + 256, 256);                             // unit counter + spare
+  o = align_up(o + 16 + 4 * (size_t)F, 256);              // unit counter + frame order
   for (int f = 0; f < F; ++f) {
-    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], splits, o);
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], splits, up, o);
     o = fl.total;
   }
   return o;
@@ -155,17 +158,17 @@ rsim_status ensure_workspace(rsim_ctx* ctx, size_t bytes, cudaStream_t st) {
 
 // Fill FrameIO entries for F frames in workspace `ws` and upload the table.
 rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pixels* frames,
-                         int F, void* const* cubes, int splits, cudaStream_t st,
+                         int F, void* const* cubes, int splits, bool use_partial, cudaStream_t st,
                          std::vector<FrameIO>& host, FrameIO** dev_table, int** counter) {
   host.assign(F, FrameIO{});
   size_t o = align_up(sizeof(FrameIO) * (size_t)F, 256);
   unsigned long long* meta = (unsigned long long*)(ws + o);
   o = align_up(o + 16 * (size_t)F, 256);
   *counter = (int*)(ws + o);
-  o = align_up(o + 256, 256);
+  o = align_up(o + 16 + 4 * (size_t)F, 256);
   for (int f = 0; f < F; ++f) {
     const rsim_pixels& px = frames[f];
-    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, px.P, splits, o);
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, px.P, splits, use_partial, o);
     o = fl.total;
     FrameIO& io = host[f];
     io.range = px.range;
@@ -184,7 +187,7 @@ rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pi
     io.sig = (float2*)(ws + fl.sig);
     io.blk_count = (int32_t*)(ws + fl.blk);
     io.meta = meta + 2 * f;
-    io.partial = splits > 1 ? (float2*)(ws + fl.partial) : nullptr;
+    io.partial = use_partial ? (float2*)(ws + fl.partial) : nullptr;
     io.splits = splits;
   }
   *dev_table = (FrameIO*)ws;
@@ -209,14 +212,16 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   std::vector<int64_t> Ps(F);
   for (int f = 0; f < F; ++f) Ps[f] = frames[f].P;
   const int splits = plan.splits;
-  if (batch_bytes(k, Ps.data(), F, splits) > ws_bytes)
+  if (batch_bytes(k, Ps.data(), F, splits, tier) > ws_bytes)
     return fail(RSIM_ERR_INVALID_ARG, "workspace too small for this request");
+  const int64_t mp = max_P(frames, F);
+  const bool use_partial = uses_partial(tier, mp, splits);
   std::vector<FrameIO> host;
   FrameIO* table = nullptr;
   int* counter = nullptr;
-  rsim_status s = stage_frames(ctx, ws, k, frames, F, cubes, splits, st, host, &table, &counter);
+  rsim_status s = stage_frames(ctx, ws, k, frames, F, cubes, splits, use_partial, st, host, &table,
+                               &counter);
   if (s != RSIM_OK) return s;
-  const int64_t mp = max_P(frames, F);
   // stage events when profiling this context's own calls
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   const bool prof = ctx->prof && status == ctx->status_dev;
@@ -229,7 +234,9 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     }
     for (int i = 0; i < 4; ++i) ev[i] = ctx->ev_pool[base + i];
     ctx->prof_calls++;
-    ctx->prof_kernels += 3 + (splits > 1 ? 1 : 0);
+    // compaction + phases (2), contraction (1, plus the frame-order kernel on tensor tiers),
+    // split reduction (1 when the partial buffer is used)
+    ctx->prof_kernels += 3 + (tier != RSIM_TIER_FP32 ? 1 : 0) + (use_partial ? 1 : 0);
     cudaEventRecord(ev[0], st);
   }
   cudaError_t e = launch_prep(k, table, F, mp, frames[0].dtype, false, status, st);
@@ -239,19 +246,19 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     e = launch_direct(k, table, F, splits, out_dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
     if (prof) cudaEventRecord(ev[2], st);
-    if (splits > 1) {
+    if (use_partial) {
       e = launch_reduce(k, table, F, splits, out_dtype, 0.f, st);
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
     }
   } else {
-    e = cudaMemsetAsync(counter, 0, 256, st);
+    e = cudaMemsetAsync(counter, 0, 16, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
-    e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, ctx->num_sms, status, counter,
-                    st);
+    e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, use_partial, ctx->num_sms, status,
+                    counter, st);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     if (prof) cudaEventRecord(ev[2], st);
-    if (splits > 1) {
+    if (use_partial) {
       const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
       e = launch_reduce(k, table, F, splits, out_dtype, scaled ? 1.f : 0.f, st);
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
@@ -320,7 +327,7 @@ rsim_status rsim_workspace_size(rsim_ctx* ctx, const rsim_radar_params* params, 
   rsim_status s = check_params(params, &k);
   if (s != RSIM_OK) return s;
   rsim_plan plan = choose_plan(ctx, tier, k, P);
-  *bytes = batch_bytes(k, &P, 1, plan.splits);
+  *bytes = batch_bytes(k, &P, 1, plan.splits, tier);
   return RSIM_OK;
 }
 
@@ -361,7 +368,7 @@ rsim_status rsim_synth_batch(rsim_ctx* ctx, const rsim_radar_params* params,
   rsim_plan plan = choose_plan(ctx, tier, k, maxp);
   std::vector<int64_t> Ps(F);
   for (int f = 0; f < F; ++f) Ps[f] = frames[f].P;
-  const size_t need = batch_bytes(k, Ps.data(), F, plan.splits);
+  const size_t need = batch_bytes(k, Ps.data(), F, plan.splits, tier);
   s = ensure_workspace(ctx, need, st);
   if (s != RSIM_OK) return s;
   return run_frames(ctx, (char*)ctx->ws, ctx->ws_bytes, k, frames, F, cubes, tier, out_dtype, plan,
@@ -380,13 +387,13 @@ rsim_status rsim_valid_indices(rsim_ctx* ctx, const rsim_pixels* pixels, int32_t
   k.Ns = 1;
   k.L = 1;
   int64_t P = pixels->P;
-  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, 1), st);
+  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, 1, RSIM_TIER_FP32), st);
   if (s != RSIM_OK) return s;
   std::vector<FrameIO> host;
   FrameIO* table = nullptr;
   int* counter = nullptr;
   void* cubes[1] = {nullptr};
-  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, st, host, &table, &counter);
+  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, st, host, &table, &counter);
   if (s != RSIM_OK) return s;
   // the index list goes straight to the caller's buffer; the count is copied after
   host[0].idx = idx;
@@ -411,13 +418,13 @@ rsim_status rsim_path_phases(rsim_ctx* ctx, const rsim_radar_params* params,
   cudaStream_t st = (cudaStream_t)stream;
   cudaSetDevice(ctx->device);
   int64_t P = pixels->P;
-  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, 1), st);
+  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, 1, RSIM_TIER_FP32), st);
   if (s != RSIM_OK) return s;
   std::vector<FrameIO> host;
   FrameIO* table = nullptr;
   int* counter = nullptr;
   void* cubes[1] = {nullptr};
-  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, st, host, &table, &counter);
+  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, st, host, &table, &counter);
   if (s != RSIM_OK) return s;
   host[0].phA = a;
   host[0].phC = cph;
@@ -477,6 +484,22 @@ rsim_status rsim_profile_read(rsim_ctx* ctx, rsim_profile* out) {
   ctx->prof_calls = 0;
   ctx->prof_kernels = 0;
   *out = p;
+  return RSIM_OK;
+}
+
+rsim_status rsim_set_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
+                          rsim_tier tier, const rsim_plan* plan) {
+  if (!ctx || !plan) return fail(RSIM_ERR_INVALID_ARG, "NULL argument");
+  if (!tier_ok(tier)) return fail(RSIM_ERR_INVALID_ARG, "unknown tier");
+  if (plan->splits < 1 || plan->splits > kMaxSplits || plan->grid < 0)
+    return fail(RSIM_ERR_INVALID_ARG, "plan splits must be in 1..64 and grid >= 0");
+  Consts k;
+  rsim_status s = check_params(params, &k);
+  if (s != RSIM_OK) return s;
+  rsim_plan p = *plan;
+  p.chunk_px = kChunkPx;
+  std::lock_guard<std::mutex> g(ctx->plan_mu);
+  ctx->plans[plan_key(tier, k, P)] = p;
   return RSIM_OK;
 }
 

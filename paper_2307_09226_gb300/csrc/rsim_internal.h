@@ -56,7 +56,7 @@ struct FrameLayout {
   size_t idx, phA, phC, phB, sig, blk, meta, partial, total;
   int64_t Pcap;
 };
-FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, size_t base);
+FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_partial, size_t base);
 
 // Launches (all asynchronous on `st`).  `frames` is a device array of F FrameIO.
 cudaError_t launch_prep(const Consts& k, const FrameIO* frames, int F, int64_t maxP, int dtype,
@@ -66,11 +66,16 @@ cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int spl
 cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
                           float scale_from_meta, cudaStream_t st);
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
-                        int out_dtype, int grid, int num_sms, unsigned* status, int* unit_counter,
-                        cudaStream_t st);
+                        int out_dtype, int grid, bool use_partial, int num_sms, unsigned* status,
+                        int* unit_counter, cudaStream_t st);
 
 // Plan rule shared by single-frame and batch paths (depends on the shape only).
 int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms);
 int units_per_split(int tier, int V, int Ns, int L);
+// Chunks accumulated in one tensor-memory accumulator before it is drained into an
+// FP32 running sum (the tensor-core accumulator rounds toward zero; see k_umma.cu).
+int group_chunks(int tier);
+// Whether a frame of P pixels goes through the split-partial buffer + reduction.
+bool uses_partial(int tier, int64_t P, int splits);
 
 }  // namespace rsim

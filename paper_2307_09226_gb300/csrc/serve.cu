@@ -260,7 +260,7 @@ rsim_status rsim_server_submit(rsim_server* s, const rsim_request* req, uint64_t
     return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tiers need an sm_103 device");
   r.plan = choose_plan(s->ctx, req->tier, r.k, req->pixels.P);
   int64_t P = req->pixels.P;
-  r.bytes = batch_bytes(r.k, &P, 1, r.plan.splits);
+  r.bytes = batch_bytes(r.k, &P, 1, r.plan.splits, req->tier);
   std::lock_guard<std::mutex> g(s->mu);
   if (s->opts.hbm_budget_bytes && r.bytes > s->opts.hbm_budget_bytes)
     return fail(RSIM_ERR_BUDGET, "request workspace exceeds the server HBM budget");

@@ -172,7 +172,7 @@ extern "C" rsim_status rsim_autotune(rsim_ctx* ctx, const rsim_radar_params* par
       p.chunk_px = kChunkPx;
       p.tuned = 1;
       int64_t PP = P;
-      s = ensure_workspace(ctx, batch_bytes(k, &PP, 1, sp), st);
+      s = ensure_workspace(ctx, batch_bytes(k, &PP, 1, sp, tier), st);
       if (s != RSIM_OK) {
         err = s;
         break;
