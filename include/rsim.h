@@ -149,6 +149,36 @@ rsim_status rsim_synth_batch(rsim_ctx* ctx, const rsim_radar_params* params,
                              const rsim_pixels* frames, int32_t F, void* const* cubes,
                              rsim_tier tier, int32_t out_dtype, rsim_stream stream);
 
+/* One-frame synthesis that allocates nothing, for callers that must not allocate
+ * device memory (a real-time processing loop whose device memory is fixed at
+ * start-up, or a host framework that owns the device memory budget and forbids
+ * libraries from calling cudaMalloc).  The paper has no counterpart: this is a
+ * deployment variant of rsim_synth.
+ *
+ * Needs no rsim_ctx.  The scratch memory (compacted pixels, phases, split partial
+ * sums, frame table, counters) is one array of 64 MiB compiled into the library;
+ * every GPU that loads the library holds it until the process exits.  A frame
+ * whose scratch would exceed 64 MiB is rejected with RSIM_ERR_BUDGET before
+ * anything is launched.  Calls no cudaMalloc, cudaFree or other allocating routine.
+ * Inputs and output are as in rsim_synth (device pointers owned by the caller); the
+ * plan is the library's default rule for the shape, so the result equals rsim_synth
+ * of a context that has no tuned plan for it.
+ *
+ * device_status: optional DEVICE pointer to a uint32 that the kernels OR their
+ * status bits into (1: a valid pixel had a non-finite field or R <= 0; 2: a
+ * device-side wait ran out of time); the caller clears it.  With NULL, a word inside
+ * the static array is used and cleared on every call.
+ *
+ * The first call on a device, with that device current, looks up the array's device
+ * address (cudaGetSymbolAddress) and caches it; make that first call before any
+ * stream capture.  All calls on a device share the one array and it keeps the last
+ * call's contents (the call clears what must start at zero), so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race: serialise them.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, OVERFLOW, BUDGET, UNSUPPORTED, CUDA. */
+rsim_status rsim_synth_static(const rsim_radar_params* params, const rsim_pixels* pixels,
+                              rsim_tier tier, void* cube, int32_t out_dtype, uint32_t* device_status,
+                              rsim_stream stream);
+
 /* Valid-pixel compaction alone (the mask step): idx receives the indices p with
  * sigma_p != 0 in ascending order (int32, capacity P), *p_valid (DEVICE int64) their
  * count.  Asynchronous on `stream`. */

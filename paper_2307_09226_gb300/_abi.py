@@ -82,6 +82,8 @@ SIGNATURES = {
                            c_void_p, c_int32, c_void_p]),
     "rsim_synth_batch": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels),
                                  c_int32, POINTER(c_void_p), c_int, c_int32, c_void_p]),
+    "rsim_synth_static": (c_int, [POINTER(rsim_radar_params), POINTER(rsim_pixels), c_int, c_void_p,
+                                  c_int32, c_void_p, c_void_p]),
     "rsim_valid_indices": (c_int, [c_void_p, POINTER(rsim_pixels), c_void_p, c_void_p, c_void_p]),
     "rsim_path_phases": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels),
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
@@ -211,6 +213,16 @@ def rsim_synth_batch(ctx, radar, frames, tier: int, cubes, stream=None):
     od = C128 if cubes[0].dtype == torch.complex128 else C64
     check(load().rsim_synth_batch(ctx, ctypes.byref(radar_params(radar)), arr, F, ptrs, int(tier), od,
                                   _stream(stream)))
+
+
+def rsim_synth_static(radar, pixels, tier: int, cube, device_status=None, stream=None):
+    """Synthesis through the allocation-free entry point (scratch compiled into the
+    library; no context).  Returns the raw status code (does not raise)."""
+    import torch
+    od = C128 if cube.dtype == torch.complex128 else C64
+    px = pixels if isinstance(pixels, rsim_pixels) else pixels_struct(pixels)
+    return int(load().rsim_synth_static(ctypes.byref(radar_params(radar)), ctypes.byref(px), int(tier),
+                                        _ptr(cube), od, _ptr(device_status), _stream(stream)))
 
 
 def rsim_valid_indices(ctx, pixels, idx, p_valid, stream=None):
