@@ -39,6 +39,29 @@ def _dist():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, device="cpu") -> float:
+    """Max of a per-rank time over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def weak_scaling_value(samples_per_rank: int, world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput in Gpath-samples/s: every rank synthesises its own frame
+    (independent units), so the job's work is world x steps frames in the slowest
+    rank's time."""
+    return samples_per_rank * world * steps / (max_ms * 1e-3) / 1e9
+
+
+def rank_seed(rank: int) -> int:
+    """Seed of the frame a rank synthesises (rank 0 runs the reference frame)."""
+    return 2 + rank
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples (200 ms) while the timed region runs."""
 
@@ -203,7 +226,7 @@ def run_gpu(args):
     import oracle  # accuracy check of the benchmarked tier, outside the timed region
     from paper_2307_09226_gb300 import _abi, device, synth
 
-    frame = synth.config2(seed=2 + rank)  # each rank its own frame (independent units)
+    frame = synth.config2(seed=rank_seed(rank))  # each rank its own frame (independent units)
     radar = frame.radar
     ctx = device.Context(local)
     px = device.upload(frame)
@@ -272,13 +295,8 @@ def run_gpu(args):
     time.sleep(0.25)
     ms, prof = time_tier(tier, args.steps, args.warmup, profile=True)
     clocks = sampler.stop()
-    step_ms = sum(ms)
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([step_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        step_ms = float(t.item())
-    value = samples * ws * args.steps / (step_ms * 1e-3) / 1e9
+    step_ms = max_over_ranks(sum(ms), device="cuda")
+    value = weak_scaling_value(samples, ws, args.steps, step_ms)
 
     # end to end through the public API: pinned host inputs -> device -> synth -> host
     host = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -301,12 +319,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if i >= args.warmup:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_total = sum(e2e_ms)
-    if ws > 1:
-        t = torch.tensor([e2e_total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = samples * ws * args.steps / (e2e_total * 1e-3) / 1e9
+    e2e_total = max_over_ranks(sum(e2e_ms), device="cuda")
+    e2e_value = weak_scaling_value(samples, ws, args.steps, e2e_total)
 
     if rank == 0:
         peaks, kind = _peaks()

@@ -1,0 +1,188 @@
+"""GPU tests of the batched path, the serving loop and the autotuner (through the C ABI).
+
+* A batch of frames gives, frame by frame, the same bits as rsim_synth of each frame
+  alone (equal pixel counts share a plan), and matches the FP64 oracle.
+* The server's results equal the alone results, whatever mix of shapes and tiers runs
+  concurrently; admission keeps the reserved workspace within the HBM budget; queued
+  requests can be cancelled; a non-finite valid pixel is reported per request.
+* The autotuner's choice is cached (in the context and in RSIM_TUNE_CACHE) and keeps
+  results within tolerance.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_09226_gb300 import synth
+from paper_2307_09226_gb300.synth import Radar
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp32": 2e-5, "split_fp16": 2e-5, "split_bf16": 2e-5, "bf16": 1e-2, "fp16": 1e-2}
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2307_09226_gb300 import _abi, device
+    ctx = device.Context(0)
+    yield torch, _abi, device, ctx
+    ctx.close()
+
+
+@pytest.mark.parametrize("tier", ["split_fp16", "fp32", "split_bf16"])
+def test_batch_equals_alone_bit_for_bit(env, tier):
+    torch, _abi, device, ctx = env
+    frames = synth.walking_batch(n_frames=8, n_az=128, n_el=128)
+    radar = frames[0].radar
+    pxs = [device.upload(f) for f in frames]
+    cubes = ctx.synth_batch(radar, pxs, tier)
+    assert ctx.sync_status() == _abi.OK
+    for f, px, cb in zip(frames, pxs, cubes):
+        alone = ctx.synth(radar, px, tier).cpu().numpy()
+        assert np.array_equal(cb.cpu().numpy(), alone), f.meta["frame"]
+    for i in (0, 5):
+        ref = oracle.cube_separable(radar, frames[i].pixels)
+        err = oracle.rel_l2(cubes[i].cpu().numpy(), ref)
+        print(f"batch {tier} frame {i}: {err:.3e}")
+        assert err <= TOL[tier]
+
+
+def test_batch_with_uneven_pixel_counts(env):
+    torch, _abi, device, ctx = env
+    radar = Radar(M=2, N=4, Ns=128, L=64)
+    frames = [synth.random_frame(radar, a, b, seed=s, mask_frac=m)
+              for a, b, s, m in [(60, 50, 1, 0.1), (10, 7, 2, 0.5), (90, 80, 3, 0.3), (33, 3, 4, 0.0)]]
+    pxs = [device.upload(p) for p in frames]
+    for tier in ("split_fp16", "fp32"):
+        cubes = ctx.synth_batch(radar, pxs, tier)
+        assert ctx.sync_status() == _abi.OK
+        for p, cb in zip(frames, cubes):
+            err = oracle.rel_l2(cb.cpu().numpy(), oracle.cube_separable(radar, p))
+            assert err <= TOL[tier], (tier, err)
+
+
+def _requests(n, seed=5):
+    reqs = synth.serving_requests(n, seed=seed, grids=(32, 48, 64), tiers=("fp32", "split_bf16", "split_fp16"))
+    return reqs
+
+
+def test_server_results_equal_alone(env):
+    torch, _abi, device, ctx = env
+    reqs = _requests(16)
+    frames = [synth.request_frame(r) for r in reqs]
+    pxs = [device.upload(f) for f in frames]
+    cubes = [device.cube_tensor(f.radar) for f in frames]
+    srv = _abi.rsim_server_create(ctx.h, slots=4)
+    try:
+        tickets = []
+        for r, f, px, cb in zip(reqs, frames, pxs, cubes):
+            tickets.append(_abi.rsim_server_submit(srv, _abi.make_request(f.radar, px, _abi.TIERS[r["tier"]], cb)))
+        for t in tickets:
+            assert _abi.rsim_server_wait(srv, t, 60000) == _abi.OK, _abi.last_error()
+        st = _abi.rsim_server_stats_get(srv)
+    finally:
+        _abi.rsim_server_destroy(srv)
+    assert st.submitted == 16 and st.completed == 16 and st.failed == 0
+    assert st.p50_ms > 0 and st.p99_ms >= st.p50_ms
+    assert st.peak_in_flight >= 2  # requests ran concurrently
+    for r, f, px, cb in zip(reqs, frames, pxs, cubes):
+        alone = ctx.synth(f.radar, px, r["tier"]).cpu().numpy()
+        got = cb.cpu().numpy()
+        assert np.array_equal(got, alone), r
+    for i in (0, 7):
+        ref = oracle.cube_separable(frames[i].radar, frames[i].pixels)
+        assert oracle.rel_l2(cubes[i].cpu().numpy(), ref) <= TOL[reqs[i]["tier"]]
+
+
+def test_server_admission_respects_budget(env):
+    torch, _abi, device, ctx = env
+    reqs = _requests(8, seed=9)
+    frames = [synth.request_frame(r) for r in reqs]
+    pxs = [device.upload(f) for f in frames]
+    cubes = [device.cube_tensor(f.radar) for f in frames]
+    need = [_abi.rsim_workspace_size(ctx.h, f.radar, f.pixels.P, _abi.TIERS[r["tier"]])
+            for r, f in zip(reqs, frames)]
+    budget = max(need) + min(need) // 2  # at most about one request at a time
+    srv = _abi.rsim_server_create(ctx.h, slots=4, hbm_budget_bytes=budget)
+    try:
+        ts = [_abi.rsim_server_submit(srv, _abi.make_request(f.radar, px, _abi.TIERS[r["tier"]], cb))
+              for r, f, px, cb in zip(reqs, frames, pxs, cubes)]
+        for t in ts:
+            assert _abi.rsim_server_wait(srv, t, 60000) == _abi.OK
+        st = _abi.rsim_server_stats_get(srv)
+        assert st.peak_reserved_bytes <= budget
+        assert st.completed == 8
+        # a request larger than the whole budget is refused at submit
+        big = Radar(M=4, N=12, Ns=512, L=256)
+        bpx = synth.random_frame(big, 512, 512, seed=1, mask_frac=0.3)
+        bcube = device.cube_tensor(big)
+        assert _abi.rsim_workspace_size(ctx.h, big, bpx.P, 0) > budget
+        with pytest.raises(_abi.RsimError) as e:
+            _abi.rsim_server_submit(srv, _abi.make_request(big, device.upload(bpx), 0, bcube))
+        assert e.value.status == _abi.ERR_BUDGET
+    finally:
+        _abi.rsim_server_destroy(srv)
+    for r, f, px, cb in zip(reqs, frames, pxs, cubes):
+        assert np.array_equal(cb.cpu().numpy(), ctx.synth(f.radar, px, r["tier"]).cpu().numpy())
+
+
+def test_server_cancel_and_errors(env):
+    torch, _abi, device, ctx = env
+    # one slot so that later requests stay queued behind a long first one
+    big = Radar(M=4, N=12, Ns=512, L=256)
+    bpx = device.upload(synth.random_frame(big, 256, 256, seed=2, mask_frac=0.3))
+    bcube = device.cube_tensor(big)
+    small = synth.parity_frame(seed=5, n_az=20, n_el=20)
+    spx = device.upload(small)
+    bad = synth.parity_frame(seed=6, n_az=20, n_el=20, mask_frac=0.0)
+    bad.pixels.vel[3] = np.inf
+    badpx = device.upload(bad)
+    srv = _abi.rsim_server_create(ctx.h, slots=1)
+    try:
+        t0 = _abi.rsim_server_submit(srv, _abi.make_request(big, bpx, _abi.TIER_FP32, bcube))
+        c1 = device.cube_tensor(small.radar)
+        t1 = _abi.rsim_server_submit(srv, _abi.make_request(small.radar, spx, _abi.TIER_FP32, c1))
+        c2 = device.cube_tensor(bad.radar)
+        t2 = _abi.rsim_server_submit(srv, _abi.make_request(bad.radar, badpx, _abi.TIER_FP32, c2))
+        assert _abi.rsim_server_cancel(srv, t1) == _abi.OK
+        assert _abi.rsim_server_wait(srv, t1, 10000) == _abi.ERR_CANCELLED
+        assert _abi.rsim_server_wait(srv, t0, 0) in (_abi.ERR_TIMEOUT, _abi.OK)
+        assert _abi.rsim_server_wait(srv, t0, 120000) in (_abi.OK, _abi.ERR_NOT_FOUND)
+        assert _abi.rsim_server_wait(srv, t2, 60000) == _abi.ERR_NONFINITE
+        assert _abi.rsim_server_wait(srv, 987654, 10) == _abi.ERR_NOT_FOUND
+        st = _abi.rsim_server_stats_get(srv)
+        assert st.cancelled == 1 and st.failed == 1
+    finally:
+        _abi.rsim_server_destroy(srv)
+
+
+def test_autotune_caches_plan(env, tmp_path):
+    torch, _abi, device, ctx = env
+    from paper_2307_09226_gb300 import device as dev
+    cache = tmp_path / "tune.json"
+    os.environ["RSIM_TUNE_CACHE"] = str(cache)
+    try:
+        c2 = dev.Context(0)
+        f = synth.parity_frame(seed=7, M=2, N=4, Ns=128, L=64, n_az=64, n_el=64)
+        plan = _abi.rsim_autotune(c2.h, f.radar, f.pixels.P, _abi.TIER_SPLIT_FP16)
+        assert plan.tuned == 1 and 1 <= plan.splits <= 64
+        got = _abi.rsim_get_plan(c2.h, f.radar, f.pixels.P, _abi.TIER_SPLIT_FP16)
+        assert (got.splits, got.grid) == (plan.splits, plan.grid)
+        data = json.loads(cache.read_text())
+        assert any(v[0] == plan.splits for v in data.values())
+        cube = c2.synth(f.radar, dev.upload(f), "split_fp16").cpu().numpy()
+        assert oracle.rel_l2(cube, oracle.cube_separable(f.radar, f.pixels)) <= 2e-5
+        c2.close()
+        c3 = dev.Context(0)  # a new context reads the cache file
+        got3 = _abi.rsim_get_plan(c3.h, f.radar, f.pixels.P, _abi.TIER_SPLIT_FP16)
+        assert got3.tuned == 1 and got3.splits == plan.splits
+        c3.close()
+    finally:
+        os.environ.pop("RSIM_TUNE_CACHE", None)
