@@ -329,6 +329,8 @@ def run_gpu(args):
         if traffic is not None:
             roof["traffic"] = traffic
         cpu_v, cores, sample, _ = _cpu_sample(frame) if ws == 1 or rank == 0 else (None, None, None, None)
+        batch = run_batch(ctx, tier, steps=max(3, min(args.steps, 10)), warmup=3) if not args.no_extras else None
+        serving = run_serving(ctx) if not args.no_extras else None
         line = {
             "metric": "cube synth Gpath-samples/s at rel err<=2e-5 vs FP64",
             "value": value, "unit": "Gpath-samples/s", "n_gpus": ws, "steps": args.steps,
@@ -351,6 +353,8 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": "Gpath-samples/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "clocks": clocks,
+            "batch": batch,
+            "serving": serving,
         }
         print(json.dumps(line))
     ctx.close()
@@ -360,17 +364,108 @@ def run_gpu(args):
     return 0
 
 
+KERNEL_SOURCES = {"fp32": "k_direct.cu", "split_fp16": "k_umma.cu", "split_bf16": "k_umma.cu",
+                  "bf16": "k_umma.cu", "fp16": "k_umma.cu"}
+
+
+def kernel_source_hash(tier):
+    import hashlib
+    p = os.path.join(ROOT, "paper_2307_09226_gb300", "csrc", KERNEL_SOURCES[tier])
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:12]
+
+
 def _load_traffic(tier):
-    """DRAM bytes per launch of the contraction kernel from the committed ncu summary."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch of the contraction kernel, from the ncu capture recorded in
+    profiles/traffic.txt (lines: tier  source-hash  bytes).  None when nothing was
+    recorded for this tier or the kernel source has changed since the capture."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(p):
         return None
-    try:
-        with open(p) as f:
-            d = json.load(f)
-        return d.get(tier)
-    except (OSError, ValueError):
-        return None
+    want = kernel_source_hash(tier)
+    with open(p) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == tier and parts[1] == want:
+                return float(parts[2])
+    return None
+
+
+def run_batch(ctx, tier, steps, warmup):
+    """Config 4: 64 walking-pedestrian frames (uneven valid-pixel counts) in one
+    rsim_synth_batch call per step; inputs resident, L2 flushed between steps."""
+    import torch
+    import oracle
+    from paper_2307_09226_gb300 import device, synth
+    frames = synth.walking_batch(n_frames=64)
+    radar = frames[0].radar
+    pxs = [device.upload(f) for f in frames]
+    cubes = [device.cube_tensor(radar) for _ in frames]
+    pvs = [int(oracle.valid_mask(f.pixels.sigma_re, f.pixels.sigma_im).sum()) for f in frames]
+    samples = sum(pvs) * radar.V * radar.Ns * radar.L
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        ctx.synth_batch(radar, pxs, tier, cubes=cubes)
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(steps):
+        flush.fill_(float(i))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.synth_batch(radar, pxs, tier, cubes=cubes)
+        b.record()
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+    t = statistics.median(ms)
+    return {"workload": "walking-64x256x256-V12-Ns256-L128", "tier": tier, "frames": len(frames),
+            "P_valid_min": min(pvs), "P_valid_max": max(pvs), "ms_per_batch": round(t, 4),
+            "value": samples / (t * 1e-3) / 1e9, "unit": "Gpath-samples/s", "steps": steps}
+
+
+def run_serving(ctx, n_requests=120, slots=4, seed=5):
+    """Config 5: Poisson stream of mixed requests (M 2-4, N 4-12, Ns 128-512, L 64-256,
+    64^2..512^2 pixels, FP32 and split-BF16 tiers) into the continuous-batching server at
+    0.7 x the measured capacity; latency is submit -> completion."""
+    import numpy as np
+    import torch
+    from paper_2307_09226_gb300 import _abi, device, synth
+    reqs = synth.serving_requests(n_requests, seed=seed)
+    frames = [synth.request_frame(r) for r in reqs]
+    pxs = [device.upload(f) for f in frames]
+    cubes = [device.cube_tensor(f.radar) for f in frames]
+    made = [_abi.make_request(f.radar, px, _abi.TIERS[r["tier"]], cb)
+            for r, f, px, cb in zip(reqs, frames, pxs, cubes)]
+    # capacity: every request once, back to back, on one server slot
+    srv = _abi.rsim_server_create(ctx.h, slots=1)
+    t0 = time.perf_counter()
+    for m in made:
+        _abi.rsim_server_wait(srv, _abi.rsim_server_submit(srv, m), -1)
+    alone_s = (time.perf_counter() - t0) / len(made)
+    _abi.rsim_server_destroy(srv)
+    rate = 0.7 / alone_s
+    rng = np.random.default_rng(seed + 1)
+    gaps = rng.exponential(1.0 / rate, len(made))
+    srv = _abi.rsim_server_create(ctx.h, slots=slots)
+    tickets = []
+    start = time.perf_counter()
+    due = start
+    for m, gap in zip(made, gaps):
+        due += gap
+        delay = due - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(_abi.rsim_server_submit(srv, m))
+    bad = sum(_abi.rsim_server_wait(srv, t, -1) != _abi.OK for t in tickets)
+    st = _abi.rsim_server_stats_get(srv)
+    _abi.rsim_server_destroy(srv)
+    torch.cuda.synchronize()
+    return {"workload": "poisson-mix-M2..4-N4..12-Ns128..512-L64..256-P4k..262k", "requests": len(made),
+            "slots": slots, "rate_req_s": round(rate, 2), "offered_load": 0.7,
+            "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),
+            "max_ms": round(st.max_ms, 3), "req_per_s": round(st.completed / max(st.busy_s, 1e-9), 2),
+            "value": st.path_samples / max(st.busy_s, 1e-9) / 1e9, "unit": "Gpath-samples/s",
+            "failed": int(st.failed) + bad, "peak_in_flight": int(st.peak_in_flight),
+            "alone_mean_ms": round(alone_s * 1e3, 3)}
 
 
 def main():
@@ -380,6 +475,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--tier", default=None, choices=[None, "fp32", "split_fp16", "split_bf16", "bf16", "fp16"])
     ap.add_argument("--impl", default="library", choices=["library", "reference"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batch (64 frames) and serving (Poisson mix) measurements")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3

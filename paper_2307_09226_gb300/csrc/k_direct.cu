@@ -139,20 +139,30 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
   }
 }
 
-// cube = scale * sum over splits s = 0, 1, ... (in this order, FP64) of partial[s].
+// Add x to the compensated sum (s, c) (Kahan): the running error of FP32 additions is
+// carried in c, so the sum of a few dozen partials is as accurate as one rounding.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
+
+// cube = scale * sum over splits s = 0, 1, ... (in this order) of partial[s], with
+// compensated FP32 additions (GB300's FP64 rate is a small fraction of its FP32 rate).
 // Loads of eight splits are issued together; the additions keep the split order.
 __global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, int splits,
                              int out_dtype, int scale_mode) {
   const FrameIO& fr = frames[blockIdx.y];
-  double scale = 1.0;
+  float scale = 1.f;
   if (scale_mode) {
     const float m = __uint_as_float((unsigned)fr.meta[1]);
-    scale = (m > 0.f) ? ldexp(1.0, ilogbf(m) + 1) : 1.0;
+    scale = (m > 0.f) ? ldexpf(1.f, ilogbf(m) + 1) : 1.f;
   }
   const float2* __restrict__ part = fr.partial;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double re = 0.0, im = 0.0;
+    float re = 0.f, im = 0.f, cre = 0.f, cim = 0.f;
     for (int s0 = 0; s0 < splits; s0 += 8) {
       float2 p[8];
 #pragma unroll
@@ -160,16 +170,18 @@ __global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, 
         p[j] = (s0 + j < splits) ? __ldcs(part + (int64_t)(s0 + j) * count + i) : make_float2(0.f, 0.f);
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
-        re += (double)p[j].x;
-        im += (double)p[j].y;
+        if (s0 + j < splits) {
+          kahan_add(re, cre, p[j].x);
+          kahan_add(im, cim, p[j].y);
+        }
       }
     }
-    re *= scale;
+    re *= scale;  // power of two: exact
     im *= scale;
     if (out_dtype == RSIM_C128)
-      reinterpret_cast<double2*>(fr.cube)[i] = make_double2(re, im);
+      reinterpret_cast<double2*>(fr.cube)[i] = make_double2((double)re, (double)im);
     else
-      reinterpret_cast<float2*>(fr.cube)[i] = make_float2((float)re, (float)im);
+      reinterpret_cast<float2*>(fr.cube)[i] = make_float2(re, im);
   }
 }
 

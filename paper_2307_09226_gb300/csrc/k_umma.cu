@@ -11,18 +11,23 @@
 // values of l).  Split-precision tiers write each operand as hi + lo 16-bit parts and
 // accumulate A_hi B_hi + A_hi B_lo + A_lo B_hi in FP32.
 //
-// One persistent CTA per SM, warp-specialised:
-//   warps 0-3  produce A for a 128-row tile straight into tensor memory (one row per
-//              thread, tcgen05.st), then drain the accumulator (tcgen05.ld) as the
-//              epilogue;
-//   warps 4-7  produce B (the shared slow-time operand of all row tiles) into shared
-//              memory in the 128-byte-swizzled K-major layout the MMA reads;
+// B (sigma x slow-time phasors) is shared by every row tile, so an operand-builder
+// kernel writes it once per frame as ready-made shared-memory images: for each
+// 32-pixel chunk, 2 NT rows of 128 B in the 128-byte-swizzled K-major layout the MMA
+// reads.  A (fast-time/channel phasors) differs for every row tile and is never
+// reused, so it is generated on chip and never touches HBM.
+//
+// The contraction runs one persistent CTA per SM, warp-specialised:
+//   warps 0-7  produce A for a 128-row tile straight into tensor memory (one row per
+//              thread, two warps per lane quarter, 16 pixels each, tcgen05.st), and
+//              drain the accumulator (tcgen05.ld) after each group of chunks;
 //   warp 8     allocates tensor memory and one thread issues tcgen05.mma
-//              (M = 128, N = 2 NT, K = 16, A from tensor memory, B from shared memory).
-// Operands are generated on chip from the FP64-derived fixed-point phases: A has no
-// reuse across CTAs and B costs as much to generate as to load, so neither goes
-// through HBM.  Stages are handed over with mbarriers; every wait is bounded in time
-// and a timeout sets a status bit instead of hanging.
+//              (M = 128, N = 2 NT, K = 16, A from tensor memory, B from shared memory);
+//   warp 9     takes work units from a device counter and bulk-copies each chunk's
+//              phases of the tile's channels into a shared-memory ring;
+//   warp 10    bulk-copies each chunk's B images into the operand stages.
+// Stages are handed over with mbarriers; every wait is bounded in time and a timeout
+// sets a status bit instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -35,7 +40,9 @@ constexpr int kStages = 3;                 // operand stages (A in TMEM, B in sm
 constexpr int kPixStages = 6;              // ring of staged per-chunk pixel phases
 constexpr int kUnitSlots = 4;              // ring of work-unit ids
 constexpr int kMaxCh = 8;                  // channels a row tile may span for staging
-constexpr int kThreads = 320;              // 10 warps
+constexpr int kAWarps = 16;                // A producers (four per tensor-memory lane quarter)
+constexpr int kAPx = kChunkPx / (kAWarps / 4);  // pixels per A warp per stage
+constexpr int kThreads = 32 * (kAWarps + 3);  // + MMA warp, pixel loader, B loader
 constexpr int kBRowsMax = 256;             // N = 2 * NT <= 256
 constexpr int kBBytes = kBRowsMax * 128;   // one 16-bit operand part of one stage
 constexpr int kStageBytes = 2 * kBBytes;   // hi + lo
@@ -43,18 +50,17 @@ constexpr int kAccCols = 256;              // accumulator columns (N <= 256 FP32
 constexpr int kTmemCols = 512;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait, then give up
 
-// Per-chunk pixel data staged by the loader warp (bulk copies from global memory).
+// Per-chunk fast-time/channel phases staged by the pixel loader (bulk copies).
 struct PixStage {
   uint32_t a[kMaxCh][kChunkPx];  // fast-time increments of the tile's channels
   uint32_t c[kMaxCh][kChunkPx];  // spatial phases of the tile's channels
-  uint32_t b[kChunkPx];          // slow-time increments
-  float2 s[kChunkPx];            // sigma
 };
 
 struct Shared {
   uint64_t a_full[kStages];
   uint64_t b_full[kStages];
-  uint64_t empty[kStages];
+  uint64_t empty[kStages];   // this CTA's MMAs are done with the stage (A may be rewritten)
+  uint64_t bempty[kStages];  // every CTA of the cluster is done with the stage (B may be rewritten)
   uint64_t pix_full[kPixStages];
   uint64_t pix_empty[kPixStages];
   uint64_t unit_full[kUnitSlots];
@@ -133,6 +139,36 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Multicast form: the bytes land at the same offset in every CTA of `mask` and
+// complete the transaction count of the barrier at the same offset there.
+__device__ __forceinline__ void bulk_g2s_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                            uint16_t mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], "
+      "%2, [%3], %4;" ::"r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
+      : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -166,25 +202,26 @@ __device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_
       : "memory");
 }
 
+// Arrive once on the barrier at the same offset in every CTA of `mask` when this
+// thread's prior tcgen05 operations complete.
+__device__ __forceinline__ void mma_commit_mc(uint64_t* b, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(b)),
+      "h"(mask)
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(b))
                : "memory");
 }
 
-#define RSIM_R32(x)                                                                              \
-  "r"(x[0]), "r"(x[1]), "r"(x[2]), "r"(x[3]), "r"(x[4]), "r"(x[5]), "r"(x[6]), "r"(x[7]),       \
-      "r"(x[8]), "r"(x[9]), "r"(x[10]), "r"(x[11]), "r"(x[12]), "r"(x[13]), "r"(x[14]),          \
-      "r"(x[15]), "r"(x[16]), "r"(x[17]), "r"(x[18]), "r"(x[19]), "r"(x[20]), "r"(x[21]),        \
-      "r"(x[22]), "r"(x[23]), "r"(x[24]), "r"(x[25]), "r"(x[26]), "r"(x[27]), "r"(x[28]),        \
-      "r"(x[29]), "r"(x[30]), "r"(x[31])
-
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
-      "%29, %30, %31, %32};" ::"r"(taddr),
-      RSIM_R32(v)
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
       : "memory");
 }
 
@@ -200,6 +237,16 @@ __device__ __forceinline__ float2 cis_q32(uint32_t ph) {
   const float ang = (float)(int32_t)ph * 1.46291807926715968e-09f;  // 2 pi / 2^32
   float s, c;
   __sincosf(ang, &s, &c);
+  return make_float2(c, s);
+}
+
+// exp(j 2 pi x) for a 2^-32-cycle phase, the fraction taken from the top 23 bits by
+// placing them in the mantissa of a float in [1, 2) (no integer-to-float conversion);
+// the quantisation to 2^-23 cycle adds at most 7.5e-7 rad.
+__device__ __forceinline__ float2 cis_q32_fast(uint32_t ph) {
+  const float x = __int_as_float(0x3F800000u | ((ph ^ 0x80000000u) >> 9)) - 1.5f;  // [-1/2, 1/2)
+  float s, c;
+  __sincosf(x * 6.28318530717958648f, &s, &c);
   return make_float2(c, s);
 }
 
@@ -223,7 +270,9 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t&
 
 struct Geo {
   int mtiles, ntiles, NT, splits, upf, group, direct, F;
-  int64_t total_units;
+  int cs;                // CTAs per cluster: consecutive row tiles sharing one B stream
+  int mgroups;           // groups of cs row tiles
+  int64_t total_units;   // cluster work units (frame, row-tile group, column tile, split)
   const int32_t* order;  // frames by decreasing valid-pixel count
 };
 
@@ -234,14 +283,17 @@ struct Unit {
 };
 
 __device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, const Consts& k,
-                                       int64_t u) {
+                                       int64_t u, int rank) {
   Unit x;
   x.f = g.order[u / g.upf];
+  // row-tile group fastest: the CTAs running at the same time share a pixel range and
+  // so the same slow-time operand images in L2
   int r = (int)(u % g.upf);
-  x.s = r % g.splits;
-  r /= g.splits;
+  const int mg = r % g.mgroups;
+  r /= g.mgroups;
   x.nt = r % g.ntiles;
-  x.mt = r / g.ntiles;
+  x.s = r / g.ntiles;
+  x.mt = mg * g.cs + rank;  // may be past the last tile: a CTA that only helps load B
   x.pv = (int64_t)frames[x.f].meta[0];
   const int64_t nch = (x.pv + kChunkPx - 1) / kChunkPx;
   x.c0 = nch * x.s / g.splits;
@@ -250,7 +302,7 @@ __device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, cons
   const int64_t r0 = (int64_t)x.mt * 128;
   const int64_t r1 = (r0 + 127 < rows ? r0 + 127 : rows - 1);
   x.v_first = (int)(r0 / k.Ns);
-  x.span = (int)(r1 / k.Ns) - x.v_first + 1;
+  x.span = (r0 < rows) ? (int)(r1 / k.Ns) - x.v_first + 1 : 0;
   return x;
 }
 
@@ -266,7 +318,7 @@ __device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity, Shared* 
   return __all_sync(0xffffffffu, mbar_wait(b, parity, sh, status));
 }
 
-// Next work unit id from the ring filled by the loader (-1: no more work).
+// Next work unit id from the ring filled by the pixel loader (-1: no more work).
 __device__ __forceinline__ bool next_unit(Shared* sh, uint32_t ui, unsigned* status, long long* u,
                                           bool warp_collective) {
   const uint32_t slot = ui % kUnitSlots, ph = (ui / kUnitSlots) & 1u;
@@ -283,6 +335,58 @@ __device__ __forceinline__ bool next_unit(Shared* sh, uint32_t ui, unsigned* sta
   return *u >= 0;
 }
 
+// ---------------------------------------------------------------------------------
+// Operand builder: B images.  For frame f, column tile nt and chunk c, writes
+//   hi: 2 NT rows x 128 B, row lt (< NT) = pixels' (Re D, -Im D) at l = nt NT + lt,
+//       row NT + lt = (Im D, Re D), with D = sigma e^{j 2 pi b l} (scaled for FP16),
+//       16-byte units placed at (unit ^ (row & 7)) as the 128-byte swizzle wants;
+//   lo: the same for the low parts of the split tiers.
+// ---------------------------------------------------------------------------------
+template <int BF, int SPLIT>
+__global__ void __launch_bounds__(256)
+build_b_images(const FrameIO* __restrict__ frames, Consts k, int NT, int scaled) {
+  const FrameIO& fr = frames[blockIdx.z];
+  const int64_t c = blockIdx.x;
+  const int nt = blockIdx.y;
+  const int64_t pv = (int64_t)fr.meta[0];
+  if (c * kChunkPx >= pv) return;
+  const float sc = sigma_scale(fr, scaled);
+  const size_t part = (size_t)2 * NT * 128;
+  unsigned char* base = fr.bimg + ((int64_t)nt * fr.bimg_nch + c) * 2 * part;
+  const int64_t q0c = c * kChunkPx;
+  for (int e = threadIdx.x; e < 2 * NT * 8; e += blockDim.x) {
+    const int row = e >> 3, cp = e & 7;
+    const int qg = cp ^ (row & 7);
+    const bool imrow = row >= NT;
+    const int l = nt * NT + (imrow ? row - NT : row);
+    const int64_t q0 = q0c + qg * 4;
+    const uint4 b4 = *reinterpret_cast<const uint4*>(fr.phB + q0);
+    const float4 s01 = *reinterpret_cast<const float4*>(fr.sig + q0);
+    const float4 s23 = *reinterpret_cast<const float4*>(fr.sig + q0 + 2);
+    const uint32_t bv[4] = {b4.x, b4.y, b4.z, b4.w};
+    const float sr[4] = {s01.x, s01.z, s23.x, s23.z};
+    const float si[4] = {s01.y, s01.w, s23.y, s23.w};
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float dre = 0.f, dim = 0.f;
+      if (l < k.L && q0 + i < pv) {
+        const float2 w = cis_q32(bv[i] * (uint32_t)l);
+        const float a = sr[i] * sc, b = si[i] * sc;
+        dre = a * w.x - b * w.y;
+        dim = a * w.y + b * w.x;
+      }
+      if (imrow)
+        split2<BF>(dim, dre, hi[i], lo[i]);
+      else
+        split2<BF>(dre, -dim, hi[i], lo[i]);
+    }
+    const size_t off = (size_t)row * 128 + cp * 16;
+    *reinterpret_cast<uint4*>(base + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+    if (SPLIT) *reinterpret_cast<uint4*>(base + part + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+  }
+}
+
 template <int BF, int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, int out_dtype,
@@ -296,28 +400,32 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int N = 2 * g.NT;
   const uint32_t idesc = idesc_f16(BF, N);
+  const uint32_t part = (uint32_t)(2 * g.NT * 128);
+  const int rank = g.cs > 1 ? (int)cluster_rank() : 0;
+  const uint16_t cmask = (uint16_t)((1u << g.cs) - 1u);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&sh->a_full[i], 128);
-      mbar_init(&sh->b_full[i], 128);
+      mbar_init(&sh->a_full[i], 32 * kAWarps);
+      mbar_init(&sh->b_full[i], 1);
       mbar_init(&sh->empty[i], 1);
+      mbar_init(&sh->bempty[i], g.cs);
     }
     for (int i = 0; i < kPixStages; ++i) {
       mbar_init(&sh->pix_full[i], 1);
-      mbar_init(&sh->pix_empty[i], 8);  // 4 A warps + 4 B warps
+      mbar_init(&sh->pix_empty[i], kAWarps);
     }
     for (int i = 0; i < kUnitSlots; ++i) {
       mbar_init(&sh->unit_full[i], 1);
-      mbar_init(&sh->unit_empty[i], 9);  // 4 A warps + 4 B warps + the MMA thread
+      mbar_init(&sh->unit_empty[i], kAWarps + 2);  // A warps, the MMA thread, the B loader
     }
     mbar_init(&sh->acc_full, 1);
-    mbar_init(&sh->acc_empty, 128);
+    mbar_init(&sh->acc_empty, 32 * kAWarps);
     mbar_init(&sh->fin, 1);
     sh->abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 8) {
+  if (warp == kAWarps) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(&sh->tmem_base)),
                  "r"(kTmemCols)
@@ -327,27 +435,31 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   fence_before();
   __syncthreads();
   fence_after();
+  if (g.cs > 1) cluster_sync();  // peers' barriers are initialised before any multicast
   const uint32_t tmem = sh->tmem_base;
   const int64_t rows_total = (int64_t)k.V * k.Ns;
 
-  if (warp < 4) {
-    // ------------- A producers + accumulator drain: thread = accumulator row -------------
-    const int r = warp * 32 + lane;
-    const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  if (warp < kAWarps) {
+    // ------- A producers + accumulator drain: thread = accumulator row, kAPx pixels -------
+    // A entries of padded pixels and of rows past the cube need no masking: the B image
+    // rows of padded pixels are zero, and rows past the cube are never written out.
+    const int quarter = warp & 3, part = warp >> 2;
+    const int r = quarter * 32 + lane;
+    const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     uint32_t kk = 0, pk = 0, gi = 0, ui = 0;
     long long u;
     bool alive = true;
     while (alive && next_unit(sh, ui++, status, &u, true)) {
-      const Unit x = decode(g, frames, k, u);
+      const Unit x = decode(g, frames, k, u, rank);
       const FrameIO& fr = frames[x.f];
       const int64_t gr = (int64_t)x.mt * 128 + r;
       const bool row_ok = gr < rows_total;
       const int v = row_ok ? (int)(gr / k.Ns) : x.v_first;
       const uint32_t n = row_ok ? (uint32_t)(gr % k.Ns) : 0u;
       const bool staged = x.span <= kMaxCh;
-      const int vl = v - x.v_first;
-      const uint32_t* pA = fr.phA + (int64_t)v * fr.Pcap;
-      const uint32_t* pC = fr.phC + (int64_t)v * fr.Pcap;
+      const int vl = row_ok ? v - x.v_first : 0;
+      const uint32_t* pA = fr.phA + (int64_t)(row_ok ? v : 0) * fr.Pcap;
+      const uint32_t* pC = fr.phC + (int64_t)(row_ok ? v : 0) * fr.Pcap;
       const float oscale = 1.f / sigma_scale(fr, scaled);
       const int l0 = x.nt * g.NT;
       int64_t g0 = x.c0;
@@ -356,19 +468,20 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         for (int64_t c = g0; c < g1; ++c, ++kk, ++pk) {
           const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
           const uint32_t ps = pk % kPixStages, pph = (pk / kPixStages) & 1u;
-          if (!warp_wait(&sh->empty[st], ph ^ 1u, sh, status) ||
-              !warp_wait(&sh->pix_full[ps], pph, sh, status)) {
+          if (!warp_wait(&sh->pix_full[ps], pph, sh, status) ||
+              !warp_wait(&sh->empty[st], ph ^ 1u, sh, status)) {
             alive = false;
             break;
           }
-          uint32_t hi[32], lo[32];
-          const int64_t q0 = c * kChunkPx;
+          uint32_t hi[kAPx], lo[kAPx];
+          const int j0 = part * kAPx;
+          const int64_t q0 = c * kChunkPx + j0;
 #pragma unroll
-          for (int j4 = 0; j4 < kChunkPx; j4 += 4) {
+          for (int j4 = 0; j4 < kAPx; j4 += 4) {
             uint4 a4, c4;
             if (staged) {
-              a4 = *reinterpret_cast<const uint4*>(&pix[ps].a[vl][j4]);
-              c4 = *reinterpret_cast<const uint4*>(&pix[ps].c[vl][j4]);
+              a4 = *reinterpret_cast<const uint4*>(&pix[ps].a[vl][j0 + j4]);
+              c4 = *reinterpret_cast<const uint4*>(&pix[ps].c[vl][j0 + j4]);
             } else {
               a4 = *reinterpret_cast<const uint4*>(pA + q0 + j4);
               c4 = *reinterpret_cast<const uint4*>(pC + q0 + j4);
@@ -377,16 +490,15 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
             const uint32_t cv[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-              float2 f = cis_q32(av[t] * n + cv[t]);
-              if (!row_ok || q0 + j4 + t >= x.pv) f = make_float2(0.f, 0.f);
+              const float2 f = cis_q32_fast(av[t] * n + cv[t]);
               split2<BF>(f.x, f.y, hi[j4 + t], lo[j4 + t]);
             }
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&sh->pix_empty[ps]);
-          const uint32_t col = tmem + lane_base + kAccCols + st * 64;
-          tmem_st32(col, hi);
-          if (SPLIT) tmem_st32(col + 32, lo);
+          const uint32_t col = tmem + lane_base + kAccCols + st * 64 + j0;
+          tmem_st8(col, hi);
+          if (SPLIT) tmem_st8(col + 32, lo);
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           fence_before();
           mbar_arrive(&sh->a_full[st]);
@@ -399,35 +511,56 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         }
         fence_after();
         const bool none = (g1 <= g0), first = (g0 == x.c0);
-        for (int j0 = 0; j0 < g.NT; j0 += 8) {
+        for (int jb = part * 8; jb < g.NT; jb += 8 * (kAWarps / 4)) {
           uint32_t re[8], im[8];
           if (!none) {
-            tmem_ld8(tmem + lane_base + j0, re);
-            tmem_ld8(tmem + lane_base + g.NT + j0, im);
+            tmem_ld8(tmem + lane_base + jb, re);
+            tmem_ld8(tmem + lane_base + g.NT + jb, im);
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           } else {
 #pragma unroll
             for (int i = 0; i < 8; ++i) re[i] = im[i] = 0u;
           }
           if (!row_ok) continue;
+          float2* dst = g.direct ? nullptr : fr.partial + (int64_t)x.s * rows_total * k.L + gr * k.L;
+          // later groups are added with reductions: no load round trip, and one thread
+          // owns each address, so its additions land in program order (deterministic)
+          const bool vec = (k.L % 2 == 0);
 #pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const int l = l0 + j0 + i;
+          for (int i = 0; i < 8; i += 2) {
+            const int l = l0 + jb + i;
             if (l >= k.L) break;
-            const int64_t o = gr * k.L + l;
-            const float a = __uint_as_float(re[i]), b = __uint_as_float(im[i]);
+            const float a0 = __uint_as_float(re[i]), b0 = __uint_as_float(im[i]);
+            const float a1 = __uint_as_float(re[i + 1]), b1 = __uint_as_float(im[i + 1]);
+            const bool two = (l + 1 < k.L);
             if (g.direct) {
-              if (out_dtype == RSIM_C128)
-                reinterpret_cast<double2*>(fr.cube)[o] = make_double2((double)a * oscale, (double)b * oscale);
-              else
-                reinterpret_cast<float2*>(fr.cube)[o] = make_float2(a * oscale, b * oscale);
-            } else {
-              float2* dst = fr.partial + (int64_t)x.s * rows_total * k.L + o;
-              if (first) {
-                *dst = make_float2(a, b);
+              const int64_t o = gr * k.L + l;
+              if (out_dtype == RSIM_C128) {
+                double2* cd = reinterpret_cast<double2*>(fr.cube);
+                cd[o] = make_double2((double)a0 * oscale, (double)b0 * oscale);
+                if (two) cd[o + 1] = make_double2((double)a1 * oscale, (double)b1 * oscale);
               } else {
-                const float2 p = *dst;
-                *dst = make_float2(p.x + a, p.y + b);
+                float2* cf = reinterpret_cast<float2*>(fr.cube);
+                cf[o] = make_float2(a0 * oscale, b0 * oscale);
+                if (two) cf[o + 1] = make_float2(a1 * oscale, b1 * oscale);
+              }
+            } else if (vec && two) {
+              float4* d4 = reinterpret_cast<float4*>(dst + l);
+              const float4 v4 = make_float4(a0, b0, a1, b1);
+              if (first)
+                *d4 = v4;
+              else
+                atomicAdd(d4, v4);
+            } else {
+              if (first)
+                dst[l] = make_float2(a0, b0);
+              else
+                atomicAdd(dst + l, make_float2(a0, b0));
+              if (two) {
+                if (first)
+                  dst[l + 1] = make_float2(a1, b1);
+                else
+                  atomicAdd(dst + l + 1, make_float2(a1, b1));
               }
             }
           }
@@ -438,74 +571,14 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         g0 = g1;
       } while (g0 < x.c1);
     }
-  } else if (warp < 8) {
-    // ------------- B producers: sigma x slow-time phasors, real-embedded -------------
-    const int t = threadIdx.x - 128;
-    uint32_t kk = 0, pk = 0, ui = 0;
-    long long u;
-    bool alive = true;
-    while (alive && next_unit(sh, ui++, status, &u, true)) {
-      const Unit x = decode(g, frames, k, u);
-      const FrameIO& fr = frames[x.f];
-      const float sc = sigma_scale(fr, scaled);
-      const int l0 = x.nt * g.NT;
-      for (int64_t c = x.c0; c < x.c1; ++c, ++kk, ++pk) {
-        const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-        const uint32_t ps = pk % kPixStages, pph = (pk / kPixStages) & 1u;
-        if (!mbar_wait(&sh->empty[st], ph ^ 1u, sh, status) ||
-            !mbar_wait(&sh->pix_full[ps], pph, sh, status)) {
-          alive = false;
-          break;
-        }
-        unsigned char* bhi = bstage + st * kStageBytes;
-        unsigned char* blo = bhi + kBBytes;
-        const int64_t q0 = c * kChunkPx;
-        for (int e = t; e < g.NT * 8; e += 128) {
-          const int lt = e % g.NT, qg = e / g.NT;
-          const int l = l0 + lt;
-          const uint4 b4 = *reinterpret_cast<const uint4*>(&pix[ps].b[qg * 4]);
-          const float4 s01 = *reinterpret_cast<const float4*>(&pix[ps].s[qg * 4]);
-          const float4 s23 = *reinterpret_cast<const float4*>(&pix[ps].s[qg * 4 + 2]);
-          const uint32_t bv[4] = {b4.x, b4.y, b4.z, b4.w};
-          const float sr[4] = {s01.x, s01.z, s23.x, s23.z};
-          const float si[4] = {s01.y, s01.w, s23.y, s23.w};
-          uint32_t rh[4], rl[4], ih[4], il[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) {
-            float dre = 0.f, dim = 0.f;
-            if (l < k.L && q0 + qg * 4 + i < x.pv) {
-              const float2 w = cis_q32(bv[i] * (uint32_t)l);
-              const float a = sr[i] * sc, b = si[i] * sc;
-              dre = a * w.x - b * w.y;
-              dim = a * w.y + b * w.x;
-            }
-            split2<BF>(dre, -dim, rh[i], rl[i]);  // row l      : (Re D, -Im D)
-            split2<BF>(dim, dre, ih[i], il[i]);   // row NT + l : (Im D,  Re D)
-          }
-          const int rre = lt, rim = g.NT + lt;
-          const uint32_t ore = rre * 128 + (((uint32_t)qg ^ (rre & 7)) << 4);
-          const uint32_t oim = rim * 128 + (((uint32_t)qg ^ (rim & 7)) << 4);
-          *reinterpret_cast<uint4*>(bhi + ore) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
-          *reinterpret_cast<uint4*>(bhi + oim) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
-          if (SPLIT) {
-            *reinterpret_cast<uint4*>(blo + ore) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
-            *reinterpret_cast<uint4*>(blo + oim) = make_uint4(il[0], il[1], il[2], il[3]);
-          }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&sh->pix_empty[ps]);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&sh->b_full[st]);
-      }
-    }
-  } else if (warp == 8) {
+  } else if (warp == kAWarps) {
     // ------------- MMA issuer (one thread) -------------
     if (lane == 0) {
       uint32_t kk = 0, gi = 0, ui = 0;
       long long u;
       bool alive = true;
       while (alive && next_unit(sh, ui++, status, &u, false)) {
-        const Unit x = decode(g, frames, k, u);
+        const Unit x = decode(g, frames, k, u, rank);
         int64_t g0 = x.c0;
         do {
           const int64_t g1 = (x.c1 < g0 + g.group) ? x.c1 : g0 + g.group;
@@ -534,6 +607,10 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
               }
             }
             mma_commit(&sh->empty[st]);
+            if (g.cs > 1)
+              mma_commit_mc(&sh->bempty[st], cmask);
+            else
+              mma_commit(&sh->bempty[st]);
           }
           if (!alive) break;
           if (g1 > g0)
@@ -548,19 +625,22 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
       mma_commit(&sh->fin);
       mbar_wait(&sh->fin, 0, sh, status);
     }
-  } else {
-    // ------------- loader: work units + bulk copies of per-chunk pixel phases -------------
+  } else if (warp == kAWarps + 1) {
+    // ------------- pixel loader: work units + bulk copies of the tile's phases -------------
     if (lane == 0) {
       uint32_t pk = 0;
       for (uint32_t ui = 0;; ++ui) {
-        const long long uu = (long long)atomicAdd(unit_counter, 1);
+        // one CTA: units from the device counter; clusters: a fixed round-robin, so
+        // every CTA of a cluster works on the same unit without exchanging ids
+        const long long uu = g.cs > 1 ? (long long)cluster_id() + (long long)ui * cluster_count()
+                                      : (long long)atomicAdd(unit_counter, 1);
         const long long u = uu < g.total_units ? uu : -1;
         const uint32_t slot = ui % kUnitSlots, uph = (ui / kUnitSlots) & 1u;
         if (!mbar_wait(&sh->unit_empty[slot], uph ^ 1u, sh, status)) break;
         *(volatile long long*)&sh->unit[slot] = u;
         mbar_arrive(&sh->unit_full[slot]);
         if (u < 0) break;
-        const Unit x = decode(g, frames, k, u);
+        const Unit x = decode(g, frames, k, u, rank);
         const FrameIO& fr = frames[x.f];
         const bool staged = x.span <= kMaxCh;
         bool alive = true;
@@ -570,27 +650,56 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
             alive = false;
             break;
           }
+          if (!staged || x.span <= 0) {
+            mbar_arrive(&sh->pix_full[ps]);
+            continue;
+          }
           const int64_t q0 = c * kChunkPx;
-          const uint32_t bytes = 4 * kChunkPx + 8 * kChunkPx + (staged ? 8u * kChunkPx * x.span : 0u);
-          mbar_expect_tx(&sh->pix_full[ps], bytes);
-          bulk_g2s(pix[ps].b, fr.phB + q0, 4 * kChunkPx, &sh->pix_full[ps]);
-          bulk_g2s(pix[ps].s, fr.sig + q0, 8 * kChunkPx, &sh->pix_full[ps]);
-          if (staged) {
-            for (int i = 0; i < x.span; ++i) {
-              const int64_t ro = (int64_t)(x.v_first + i) * fr.Pcap + q0;
-              bulk_g2s(pix[ps].a[i], fr.phA + ro, 4 * kChunkPx, &sh->pix_full[ps]);
-              bulk_g2s(pix[ps].c[i], fr.phC + ro, 4 * kChunkPx, &sh->pix_full[ps]);
-            }
+          mbar_expect_tx(&sh->pix_full[ps], 8u * kChunkPx * x.span);
+          for (int i = 0; i < x.span; ++i) {
+            const int64_t ro = (int64_t)(x.v_first + i) * fr.Pcap + q0;
+            bulk_g2s(pix[ps].a[i], fr.phA + ro, 4 * kChunkPx, &sh->pix_full[ps]);
+            bulk_g2s(pix[ps].c[i], fr.phC + ro, 4 * kChunkPx, &sh->pix_full[ps]);
           }
         }
         if (!alive) break;
+      }
+    }
+  } else {
+    // ------------- B loader: bulk copies of the chunk's B images into the operand stage -------------
+    if (lane == 0) {
+      uint32_t kk = 0, ui = 0;
+      long long u;
+      bool alive = true;
+      while (alive && next_unit(sh, ui++, status, &u, false)) {
+        const Unit x = decode(g, frames, k, u, rank);
+        const FrameIO& fr = frames[x.f];
+        for (int64_t c = x.c0; c < x.c1; ++c, ++kk) {
+          const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
+          if (!mbar_wait(&sh->bempty[st], ph ^ 1u, sh, status)) {
+            alive = false;
+            break;
+          }
+          const unsigned char* src = fr.bimg + ((int64_t)x.nt * fr.bimg_nch + c) * 2 * part;
+          unsigned char* dst = bstage + st * kStageBytes;
+          mbar_expect_tx(&sh->b_full[st], SPLIT ? 2 * part : part);
+          if (g.cs > 1) {
+            const uint32_t slice = part / g.cs, off = slice * rank;
+            bulk_g2s_mc(dst + off, src + off, slice, &sh->b_full[st], cmask);
+            if (SPLIT) bulk_g2s_mc(dst + kBBytes + off, src + part + off, slice, &sh->b_full[st], cmask);
+          } else {
+            bulk_g2s(dst, src, part, &sh->b_full[st]);
+            if (SPLIT) bulk_g2s(dst + kBBytes, src + part, part, &sh->b_full[st]);
+          }
+        }
       }
     }
   }
 
   fence_before();
   __syncthreads();
-  if (warp == 8) {
+  if (g.cs > 1) cluster_sync();  // no peer still multicasts into this CTA's memory
+  if (warp == kAWarps) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
                  : "memory");
@@ -612,28 +721,67 @@ __global__ void order_frames(const FrameIO* __restrict__ frames, int F, int32_t*
 }
 
 template <int BF, int SPLIT>
-cudaError_t launch_t(const Consts& k, const FrameIO* frames, const Geo& g, int grid, int scaled,
-                     int out_dtype, unsigned* status, int* counter, cudaStream_t st) {
+cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, int num_sms, int scaled,
+                     int out_dtype, int64_t nch_max, unsigned* status, int* counter, cudaStream_t st) {
+  cudaError_t e;
+  if (nch_max > 0) {
+    build_b_images<BF, SPLIT><<<dim3((unsigned)nch_max, g.ntiles, g.F), 256, 0, st>>>(frames, k, g.NT, scaled);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int smem = kStages * kStageBytes + kPixStages * (int)sizeof(PixStage) + (int)sizeof(Shared) + 1024;
   auto fn = umma_contract<BF, SPLIT>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  fn<<<grid, kThreads, smem, st>>>(frames, k, g, scaled, out_dtype, status, counter);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  int clusters;
+  if (g.cs > 1) {
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = g.cs;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // the schedule is static per cluster, so launch only clusters that fit at once
+    cfg.gridDim = dim3(g.cs * (num_sms / g.cs));
+    int fit = 0;
+    e = cudaOccupancyMaxActiveClusters(&fit, (void*)fn, &cfg);
+    if (e != cudaSuccess || fit < 1) {
+      cudaGetLastError();
+      fit = 1;
+    }
+    clusters = grid > 0 ? grid / g.cs : fit;
+    if (clusters > fit) clusters = fit;
+  } else {
+    clusters = grid > 0 ? grid : num_sms;
+  }
+  if (clusters < 1) clusters = 1;
+  if (clusters > g.total_units) clusters = (int)g.total_units;
+  cfg.gridDim = dim3(clusters * g.cs);
+  return cudaLaunchKernelEx(&cfg, fn, frames, k, g, scaled, out_dtype, status, counter);
 }
 
 }  // namespace
 
+int tile_nt(int L) { return L >= 128 ? 128 : ((L + 7) / 8) * 8; }
+
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
-                        int out_dtype, int grid, bool use_partial, int num_sms, unsigned* status,
-                        int* unit_counter, cudaStream_t st) {
+                        int out_dtype, int grid, int cluster, bool use_partial, int num_sms,
+                        int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st) {
   Geo g;
   const int64_t rows = (int64_t)k.V * k.Ns;
-  g.NT = k.L >= 128 ? 128 : ((k.L + 7) / 8) * 8;
+  g.NT = tile_nt(k.L);
   g.ntiles = (k.L + g.NT - 1) / g.NT;
   g.mtiles = (int)((rows + 127) / 128);
+  g.cs = (cluster == 2 || cluster == 4 || cluster == 8) ? cluster : 1;
+  if (g.cs > g.mtiles) g.cs = g.mtiles >= 4 ? 4 : (g.mtiles >= 2 ? 2 : 1);
+  g.mgroups = (g.mtiles + g.cs - 1) / g.cs;
   g.splits = splits;
-  g.upf = g.mtiles * g.ntiles * splits;
+  g.upf = g.mgroups * g.ntiles * splits;
   g.group = group_chunks(tier);
   g.direct = use_partial ? 0 : 1;
   g.F = F;
@@ -645,17 +793,16 @@ cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int split
   order_frames<<<1, 256, 0, st>>>(frames, F, order);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int blocks = grid > 0 ? grid : num_sms;
-  if (blocks > g.total_units) blocks = (int)g.total_units;
+  const int64_t nch_max = (max_p + kChunkPx - 1) / kChunkPx;
   switch (tier) {
     case RSIM_TIER_BF16:
-      return launch_t<1, 0>(k, frames, g, blocks, 0, out_dtype, status, unit_counter, st);
+      return launch_t<1, 0>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, status, unit_counter, st);
     case RSIM_TIER_SPLIT_BF16:
-      return launch_t<1, 1>(k, frames, g, blocks, 0, out_dtype, status, unit_counter, st);
+      return launch_t<1, 1>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, status, unit_counter, st);
     case RSIM_TIER_SPLIT_FP16:
-      return launch_t<0, 1>(k, frames, g, blocks, 1, out_dtype, status, unit_counter, st);
+      return launch_t<0, 1>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, status, unit_counter, st);
     case RSIM_TIER_FP16:
-      return launch_t<0, 0>(k, frames, g, blocks, 1, out_dtype, status, unit_counter, st);
+      return launch_t<0, 0>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, status, unit_counter, st);
     default:
       return cudaErrorInvalidValue;
   }

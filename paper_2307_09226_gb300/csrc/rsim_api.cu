@@ -39,7 +39,8 @@ static bool mul_ok(int64_t a, int64_t b, int64_t* out) {
   return true;
 }
 
-FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_partial, size_t base) {
+FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_partial, bool tensor,
+                         size_t base) {
   FrameLayout fl{};
   const int64_t Pcap = std::max<int64_t>(64, (P + 63) / 64 * 64);
   fl.Pcap = Pcap;
@@ -53,6 +54,15 @@ FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_p
   fl.meta = 0;     // lives in the batch header
   fl.partial = o;
   if (use_partial) o = align_up(o + 8 * (size_t)splits * V * Ns * L, 256);
+  // slow-time operand images: [column tile][chunk][hi, lo][2 NT rows x 128 B]
+  fl.bimg_nch = Pcap / kChunkPx;
+  fl.bimg = align_up(o, 1024);
+  o = fl.bimg;
+  if (tensor) {
+    const int nt = tile_nt(L);
+    const int ntiles = (L + nt - 1) / nt;
+    o = align_up(o + (size_t)ntiles * fl.bimg_nch * 2 * bimg_part_bytes(L), 256);
+  }
   fl.total = o;
   return fl;
 }
@@ -104,6 +114,9 @@ std::string plan_key(int tier, const Consts& k, int64_t P) {
   return b;
 }
 
+// CTAs per cluster of the tensor-core contraction: plan.variant, 0 = the default (1).
+int plan_cluster(const rsim_plan& p) { return p.variant > 0 ? p.variant : 1; }
+
 rsim_plan choose_plan(rsim_ctx* ctx, int tier, const Consts& k, int64_t P) {
   {
     std::lock_guard<std::mutex> g(ctx->plan_mu);
@@ -128,7 +141,7 @@ size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits, int tie
   o = align_up(o + 16 * (size_t)F, 256);                  // meta
   o = align_up(o + 16 + 4 * (size_t)F, 256);              // unit counter + frame order
   for (int f = 0; f < F; ++f) {
-    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], splits, up, o);
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], splits, up, tier != RSIM_TIER_FP32, o);
     o = fl.total;
   }
   return o;
@@ -158,8 +171,9 @@ rsim_status ensure_workspace(rsim_ctx* ctx, size_t bytes, cudaStream_t st) {
 
 // Fill FrameIO entries for F frames in workspace `ws` and upload the table.
 rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pixels* frames,
-                         int F, void* const* cubes, int splits, bool use_partial, cudaStream_t st,
-                         std::vector<FrameIO>& host, FrameIO** dev_table, int** counter) {
+                         int F, void* const* cubes, int splits, bool use_partial, bool tensor,
+                         cudaStream_t st, std::vector<FrameIO>& host, FrameIO** dev_table,
+                         int** counter) {
   host.assign(F, FrameIO{});
   size_t o = align_up(sizeof(FrameIO) * (size_t)F, 256);
   unsigned long long* meta = (unsigned long long*)(ws + o);
@@ -168,7 +182,7 @@ rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pi
   o = align_up(o + 16 + 4 * (size_t)F, 256);
   for (int f = 0; f < F; ++f) {
     const rsim_pixels& px = frames[f];
-    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, px.P, splits, use_partial, o);
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, px.P, splits, use_partial, tensor, o);
     o = fl.total;
     FrameIO& io = host[f];
     io.range = px.range;
@@ -188,6 +202,8 @@ rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pi
     io.blk_count = (int32_t*)(ws + fl.blk);
     io.meta = meta + 2 * f;
     io.partial = use_partial ? (float2*)(ws + fl.partial) : nullptr;
+    io.bimg = tensor ? (unsigned char*)(ws + fl.bimg) : nullptr;
+    io.bimg_nch = fl.bimg_nch;
     io.splits = splits;
   }
   *dev_table = (FrameIO*)ws;
@@ -219,8 +235,8 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   std::vector<FrameIO> host;
   FrameIO* table = nullptr;
   int* counter = nullptr;
-  rsim_status s = stage_frames(ctx, ws, k, frames, F, cubes, splits, use_partial, st, host, &table,
-                               &counter);
+  rsim_status s = stage_frames(ctx, ws, k, frames, F, cubes, splits, use_partial,
+                               tier != RSIM_TIER_FP32, st, host, &table, &counter);
   if (s != RSIM_OK) return s;
   // stage events when profiling this context's own calls
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -253,8 +269,8 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   } else {
     e = cudaMemsetAsync(counter, 0, 16, st);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
-    e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, use_partial, ctx->num_sms, status,
-                    counter, st);
+    e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, plan_cluster(plan), use_partial,
+                    ctx->num_sms, mp, status, counter, st);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     if (prof) cudaEventRecord(ev[2], st);
@@ -393,7 +409,8 @@ rsim_status rsim_valid_indices(rsim_ctx* ctx, const rsim_pixels* pixels, int32_t
   FrameIO* table = nullptr;
   int* counter = nullptr;
   void* cubes[1] = {nullptr};
-  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, st, host, &table, &counter);
+  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, false, st, host, &table,
+                   &counter);
   if (s != RSIM_OK) return s;
   // the index list goes straight to the caller's buffer; the count is copied after
   host[0].idx = idx;
@@ -424,7 +441,8 @@ rsim_status rsim_path_phases(rsim_ctx* ctx, const rsim_radar_params* params,
   FrameIO* table = nullptr;
   int* counter = nullptr;
   void* cubes[1] = {nullptr};
-  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, st, host, &table, &counter);
+  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, false, st, host, &table,
+                   &counter);
   if (s != RSIM_OK) return s;
   host[0].phA = a;
   host[0].phC = cph;

@@ -11,7 +11,7 @@
 namespace rsim {
 
 constexpr int kChunkPx = 32;        // pixels per pipeline stage / K-chunk (64 real K)
-constexpr int kPrepTile = 1024;     // pixels per block of the compaction kernels
+constexpr int kPrepTile = 256;      // pixels per block of the compaction kernels
 constexpr int kPrepThreads = 256;
 constexpr int kMaxSplits = 64;
 
@@ -44,6 +44,8 @@ struct FrameIO {
   int32_t* blk_count;         // [ceil(P / kPrepTile)] valid pixels per prep block
   unsigned long long* meta;   // [0] P_valid, [1] max(|re|,|im|) of sigma as float bits
   float2* partial;            // [splits][V*Ns][L] split partial sums (NULL if splits == 1)
+  unsigned char* bimg;        // tensor tiers: slow-time operand as shared-memory images
+  int64_t bimg_nch;           // chunk capacity of bimg per column tile
   int32_t splits;             // pixel splits of the contraction
   int32_t pad;
 };
@@ -53,10 +55,15 @@ enum : unsigned { kStatusNonfinite = 1u, kStatusTimeout = 2u };
 
 // Workspace slices of one frame, as byte offsets from a base pointer.
 struct FrameLayout {
-  size_t idx, phA, phC, phB, sig, blk, meta, partial, total;
-  int64_t Pcap;
+  size_t idx, phA, phC, phB, sig, blk, meta, partial, bimg, total;
+  int64_t Pcap, bimg_nch;
 };
-FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_partial, size_t base);
+FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_partial, bool tensor,
+                         size_t base);
+// Columns of l per tensor-core column tile, and the bytes of one 16-bit part of one
+// chunk's slow-time operand image (2 NT rows of 128 B).
+int tile_nt(int L);
+inline size_t bimg_part_bytes(int L) { return (size_t)2 * tile_nt(L) * 128; }
 
 // Launches (all asynchronous on `st`).  `frames` is a device array of F FrameIO.
 cudaError_t launch_prep(const Consts& k, const FrameIO* frames, int F, int64_t maxP, int dtype,
@@ -65,9 +72,11 @@ cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int spl
                           int out_dtype, cudaStream_t st);
 cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
                           float scale_from_meta, cudaStream_t st);
+// cluster: CTAs per thread-block cluster that share the slow-time operand by
+// multicast (1, 2, 4 or 8).
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
-                        int out_dtype, int grid, bool use_partial, int num_sms, unsigned* status,
-                        int* unit_counter, cudaStream_t st);
+                        int out_dtype, int grid, int cluster, bool use_partial, int num_sms,
+                        int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st);
 
 // Plan rule shared by single-frame and batch paths (depends on the shape only).
 int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms);

@@ -80,7 +80,7 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   const size_t off_table = o;   o = up256(o + sizeof(FrameIO));
   const size_t off_meta = o;    o = up256(o + 16);
   const size_t off_counter = o; o = up256(o + 16 + 4);
-  FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P, splits, use_partial, o);
+  FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P, splits, use_partial, tier != RSIM_TIER_FP32, o);
   o = fl.total;
   const size_t off_status = o;  o = up256(o + 4);
   if (o > kStaticWsBytes)
@@ -112,6 +112,8 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   io.blk_count = (int32_t*)(ws + fl.blk);
   io.meta = (unsigned long long*)(ws + off_meta);
   io.partial = use_partial ? (float2*)(ws + fl.partial) : nullptr;
+  io.bimg = tier != RSIM_TIER_FP32 ? (unsigned char*)(ws + fl.bimg) : nullptr;
+  io.bimg_nch = fl.bimg_nch;
   io.splits = splits;
   FrameIO* table = (FrameIO*)(ws + off_table);
   int* counter = (int*)(ws + off_counter);
@@ -130,7 +132,8 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
     if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
     if (use_partial) e = launch_reduce(k, table, 1, splits, out_dtype, 0.f, st);
   } else {
-    e = launch_umma(k, table, 1, splits, tier, out_dtype, 0, use_partial, sms, status, counter, st);
+    e = launch_umma(k, table, 1, splits, tier, out_dtype, 0, 1, use_partial, sms, P, status,
+                    counter, st);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
