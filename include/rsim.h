@@ -91,7 +91,14 @@ typedef struct {
   double t_b;      /* chirp duration [s] */
   double t_slow;   /* TDM block period [s]; <= 0 selects M * t_b */
   double c;        /* propagation speed [m/s]; <= 0 selects 299792458 */
+  int32_t flags;   /* RSIM_FLAG_* bits; 0 = the model of Eq. 1/Eq. 2 as stated */
+  int32_t reserved;
 } rsim_radar_params;
+
+/* Add the TDM motion phase: Tx m transmits in slot m of each block, so a moving pixel's
+ * Doppler also turns the phase by -f_D m T_b across the Tx slots (a per-(pixel, channel)
+ * constant added to phi).  Eq. 1 omits it (every Tx is taken at the block start). */
+#define RSIM_FLAG_TDM_MOTION 1
 
 /* One frame's render buffers: six arrays of P elements, flattened [el][az]
  * (structure of arrays), all of element type `dtype`.  sigma = (sigma_re, sigma_im)

@@ -26,7 +26,9 @@ Readings of the paper that this code takes (where it is silent or garbled):
   * the per-pixel strength is a complex amplitude, constant over m, n, l;
   * the range term uses the per-channel path range R_{p,v} of Eq. 1 and the
     spatial term is the carrier phase of the excess path 2 (R_{p,v} - R_p) / lam;
-  * the cube is stored [V][N_s][L].
+  * the cube is stored [V][N_s][L];
+  * optional TDM motion term (off by default, Eq. 1 has none): Tx m transmits in slot m
+    of each block, so phi gains -f_D,p * m * T_b with m = v // N.
 
 Two forms of the same sum:
   * ``cube_literal`` evaluates every term with its own cos/sin (the sum as written);
@@ -47,7 +49,8 @@ def _params(radar):
     t_slow = float(radar.t_slow) if radar.t_slow > 0 else radar.M * float(radar.t_b)
     return dict(M=int(radar.M), N=int(radar.N), Ns=int(radar.Ns), L=int(radar.L), lam=lam,
                 d_rx=d_rx, mu=float(radar.mu), fs=float(radar.fs), t_slow=t_slow,
-                c=float(radar.c))
+                c=float(radar.c), t_b=float(radar.t_b),
+                tdm=bool(getattr(radar, "tdm_motion", False)))
 
 
 def valid_mask(sigma_re, sigma_im):
@@ -86,9 +89,16 @@ def phase_cycles(radar, px, v, n, l):
     t = path_terms(radar, px)
     p = t["params"]
     fast = 2.0 * p["mu"] * t["R_pv"][v] / p["c"] * n / p["fs"]
-    spatial = v * p["d_rx"] * t["u"] / p["lam"]
+    spatial = v * p["d_rx"] * t["u"] / p["lam"] + _tdm(p, t, v)
     slow = -t["fD"] * l * p["t_slow"]
     return fast + spatial + slow
+
+
+def _tdm(p, t, v):
+    """TDM motion phase of channel v (cycles): -f_D * m * T_b for Tx slot m = v // N."""
+    if not p["tdm"]:
+        return 0.0
+    return -t["fD"] * (v // p["N"]) * p["t_b"]
 
 
 def _pairwise_sum(x):
@@ -124,7 +134,8 @@ def cube_literal(radar, px):
             sl = slice(s, min(Pv, s + chunk))
             # phi[p, n, l] for this channel and this slice of pixels
             fast = (2.0 * p["mu"] * t["R_pv"][v, sl] / p["c"] / p["fs"])[:, None, None] * n[None, :, None]
-            spatial = (v * p["d_rx"] * t["u"][sl] / p["lam"])[:, None, None]
+            spatial = (v * p["d_rx"] * t["u"][sl] / p["lam"]
+                       + (_tdm(p, t, v)[sl] if p["tdm"] else 0.0))[:, None, None]
             slow = -(t["fD"][sl] * p["t_slow"])[:, None, None] * l[None, None, :]
             phi = fast + spatial + slow
             phi = phi - np.round(phi)
@@ -157,7 +168,7 @@ def cube_separable(radar, px, channels=None):
     D = t["sigma"][:, None] * np.exp(2j * np.pi * slow)  # [Pv, L]
     for i, v in enumerate(chans):
         fast = (2.0 * p["mu"] * t["R_pv"][v] / p["c"] / p["fs"])[:, None] * n[None, :]
-        fast = fast + (v * p["d_rx"] * t["u"] / p["lam"])[:, None]
+        fast = fast + (v * p["d_rx"] * t["u"] / p["lam"] + _tdm(p, t, v))[:, None]
         fast = fast - np.round(fast)
         F = np.exp(2j * np.pi * fast)  # [Pv, Ns]
         out[i] = F.T @ D
@@ -178,7 +189,7 @@ def cube_entries(radar, px, entries):
         return out
     for i, (v, n, l) in enumerate(ent):
         phi = (2.0 * p["mu"] * t["R_pv"][v] / p["c"] * n / p["fs"]
-               + v * p["d_rx"] * t["u"] / p["lam"]
+               + v * p["d_rx"] * t["u"] / p["lam"] + _tdm(p, t, v)
                - t["fD"] * l * p["t_slow"])
         phi = phi - np.round(phi)
         term = t["sigma"] * (np.cos(2 * np.pi * phi) + 1j * np.sin(2 * np.pi * phi))

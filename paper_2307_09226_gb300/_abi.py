@@ -22,6 +22,7 @@ TIER_FP32, TIER_BF16, TIER_SPLIT_BF16, TIER_SPLIT_FP16, TIER_FP16 = range(5)
 TIERS = {"fp32": TIER_FP32, "bf16": TIER_BF16, "split_bf16": TIER_SPLIT_BF16,
          "split_fp16": TIER_SPLIT_FP16, "fp16": TIER_FP16}
 F32, F64 = 0, 1
+FLAG_TDM_MOTION = 1
 C64, C128 = 0, 1
 
 
@@ -34,7 +35,8 @@ class RsimError(RuntimeError):
 class rsim_radar_params(Structure):
     _fields_ = [("M", c_int32), ("N", c_int32), ("Ns", c_int32), ("L", c_int32),
                 ("lambda_", c_double), ("d_rx", c_double), ("mu", c_double), ("fs", c_double),
-                ("t_b", c_double), ("t_slow", c_double), ("c", c_double)]
+                ("t_b", c_double), ("t_slow", c_double), ("c", c_double),
+                ("flags", c_int32), ("reserved", c_int32)]
 
 
 class rsim_pixels(Structure):
@@ -135,9 +137,10 @@ def check(status: int):
 
 def radar_params(radar) -> rsim_radar_params:
     """Marshal a ``synth.Radar`` (or anything with the same attributes)."""
+    flags = FLAG_TDM_MOTION if getattr(radar, "tdm_motion", False) else 0
     return rsim_radar_params(int(radar.M), int(radar.N), int(radar.Ns), int(radar.L),
                              float(radar.lam), float(radar.d_rx), float(radar.mu), float(radar.fs),
-                             float(radar.t_b), float(radar.t_slow), float(radar.c))
+                             float(radar.t_b), float(radar.t_slow), float(radar.c), flags, 0)
 
 
 def pixels_struct(t) -> rsim_pixels:

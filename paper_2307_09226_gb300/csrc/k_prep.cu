@@ -10,7 +10,7 @@
 // integer product a * n mod 2^32: no phase of tens of cycles is ever formed in FP32.
 //
 // Two kernels, one grid row per frame:
-//   prep_count   - valid pixels per 1024-pixel tile;
+//   prep_count   - valid pixels per 256-pixel tile;
 //   prep_scatter - tile offset = sum of earlier tile counts, ordered in-tile rank by
 //                  warp ballots, then writes the index and the path phases.
 // Both are deterministic (no atomics decide positions).
@@ -119,13 +119,14 @@ prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigne
         double s_re = (double)sre[p], s_im = (double)sim[p];
         const bool ok = isfinite(r) && r > 0.0 && isfinite(a) && isfinite(e) && isfinite(w) &&
                         isfinite(s_re) && isfinite(s_im);
-        uint64_t A0 = 0, dA = 0, G = 0, Bq = 0;
+        uint64_t A0 = 0, dA = 0, G = 0, Bq = 0, Bm = 0;
         if (ok) {
           const double u = cos(e) * sin(a);       // direction cosine
           A0 = frac_u64(k.k_a0 * r);              // 2 mu R_p / (c F_s)
           dA = frac_u64(k.k_da * u);              // mu d_rx u / (c F_s): per channel index
           G = frac_u64(k.k_g * u);                // d_rx u / lambda: per channel index
           Bq = frac_u64(k.k_b * w);               // -2 vel T_slow / lambda
+          Bm = frac_u64(k.k_m * w);               // -2 vel T_b / lambda per Tx slot (or 0)
         } else {
           atomicOr(status, kStatusNonfinite);
           s_re = 0.0;
@@ -134,7 +135,7 @@ prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigne
         for (int ch = 0; ch < k.V; ++ch) {
           const uint64_t vv = (uint64_t)ch;
           fr.phA[(int64_t)ch * fr.Pcap + q] = top32(A0 + vv * dA);
-          fr.phC[(int64_t)ch * fr.Pcap + q] = top32(vv * G);
+          fr.phC[(int64_t)ch * fr.Pcap + q] = top32(vv * G + (uint64_t)(ch / k.N) * Bm);
         }
         fr.phB[q] = top32(Bq);
         const float fr_re = (float)s_re, fr_im = (float)s_im;

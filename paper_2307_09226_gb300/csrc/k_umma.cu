@@ -36,12 +36,14 @@
 namespace rsim {
 namespace {
 
-constexpr int kStages = 3;                 // operand stages (A in TMEM, B in smem)
+constexpr int kAStages = 4;                // A stages in tensor memory (64 columns each)
+constexpr int kStages = 3;                 // B stages in shared memory (64 KB each)
 constexpr int kPixStages = 6;              // ring of staged per-chunk pixel phases
 constexpr int kUnitSlots = 4;              // ring of work-unit ids
 constexpr int kMaxCh = 8;                  // channels a row tile may span for staging
-constexpr int kAWarps = 16;                // A producers (four per tensor-memory lane quarter)
-constexpr int kAPx = kChunkPx / (kAWarps / 4);  // pixels per A warp per stage
+constexpr int kAWarps = 16;                // A producers: two groups that take alternate stages
+constexpr int kAGroupWarps = kAWarps / 2;  // 8 warps per group, two per lane quarter
+constexpr int kAPx = kChunkPx / (kAGroupWarps / 4);  // pixels per A warp per stage
 constexpr int kThreads = 32 * (kAWarps + 3);  // + MMA warp, pixel loader, B loader
 constexpr int kBRowsMax = 256;             // N = 2 * NT <= 256
 constexpr int kBBytes = kBRowsMax * 128;   // one 16-bit operand part of one stage
@@ -57,10 +59,10 @@ struct PixStage {
 };
 
 struct Shared {
-  uint64_t a_full[kStages];
+  uint64_t a_full[kAStages];
+  uint64_t empty[kAStages];  // this CTA's MMAs are done with the A stage (it may be rewritten)
   uint64_t b_full[kStages];
-  uint64_t empty[kStages];   // this CTA's MMAs are done with the stage (A may be rewritten)
-  uint64_t bempty[kStages];  // every CTA of the cluster is done with the stage (B may be rewritten)
+  uint64_t bempty[kStages];  // every CTA of the cluster is done with the B stage
   uint64_t pix_full[kPixStages];
   uint64_t pix_empty[kPixStages];
   uint64_t unit_full[kUnitSlots];
@@ -218,10 +220,12 @@ __device__ __forceinline__ void mma_commit(uint64_t* b) {
                : "memory");
 }
 
-__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&v)[8]) {
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
   asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
       : "memory");
 }
 
@@ -405,15 +409,17 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   const uint16_t cmask = (uint16_t)((1u << g.cs) - 1u);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kStages; ++i) {
-      mbar_init(&sh->a_full[i], 32 * kAWarps);
-      mbar_init(&sh->b_full[i], 1);
+    for (int i = 0; i < kAStages; ++i) {
+      mbar_init(&sh->a_full[i], 32 * kAGroupWarps);
       mbar_init(&sh->empty[i], 1);
+    }
+    for (int i = 0; i < kStages; ++i) {
+      mbar_init(&sh->b_full[i], 1);
       mbar_init(&sh->bempty[i], g.cs);
     }
     for (int i = 0; i < kPixStages; ++i) {
       mbar_init(&sh->pix_full[i], 1);
-      mbar_init(&sh->pix_empty[i], kAWarps);
+      mbar_init(&sh->pix_empty[i], kAGroupWarps);
     }
     for (int i = 0; i < kUnitSlots; ++i) {
       mbar_init(&sh->unit_full[i], 1);
@@ -443,7 +449,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
     // ------- A producers + accumulator drain: thread = accumulator row, kAPx pixels -------
     // A entries of padded pixels and of rows past the cube need no masking: the B image
     // rows of padded pixels are zero, and rows past the cube are never written out.
-    const int quarter = warp & 3, part = warp >> 2;
+    const int quarter = warp & 3, part = (warp >> 2) & 1, group = warp >> 3;
     const int r = quarter * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     uint32_t kk = 0, pk = 0, gi = 0, ui = 0;
@@ -466,7 +472,8 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
       do {
         const int64_t g1 = (x.c1 < g0 + g.group) ? x.c1 : g0 + g.group;
         for (int64_t c = g0; c < g1; ++c, ++kk, ++pk) {
-          const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
+          if ((int)(kk & 1u) != group) continue;  // the other group makes this stage
+          const uint32_t st = kk % kAStages, ph = (kk / kAStages) & 1u;
           const uint32_t ps = pk % kPixStages, pph = (pk / kPixStages) & 1u;
           if (!warp_wait(&sh->pix_full[ps], pph, sh, status) ||
               !warp_wait(&sh->empty[st], ph ^ 1u, sh, status)) {
@@ -496,9 +503,10 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           }
           __syncwarp();
           if (lane == 0) mbar_arrive(&sh->pix_empty[ps]);
+          static_assert(kAPx == 16, "one x16 tensor-memory store per operand part");
           const uint32_t col = tmem + lane_base + kAccCols + st * 64 + j0;
-          tmem_st8(col, hi);
-          if (SPLIT) tmem_st8(col + 32, lo);
+          tmem_st16(col, hi);
+          if (SPLIT) tmem_st16(col + 32, lo);
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           fence_before();
           mbar_arrive(&sh->a_full[st]);
@@ -511,7 +519,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         }
         fence_after();
         const bool none = (g1 <= g0), first = (g0 == x.c0);
-        for (int jb = part * 8; jb < g.NT; jb += 8 * (kAWarps / 4)) {
+        for (int jb = ((warp >> 2) & 3) * 8; jb < g.NT; jb += 8 * (kAWarps / 4)) {
           uint32_t re[8], im[8];
           if (!none) {
             tmem_ld8(tmem + lane_base + jb, re);
@@ -589,13 +597,14 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           fence_after();
           uint32_t accum = 0;
           for (int64_t c = g0; c < g1; ++c, ++kk) {
+            const uint32_t sa = kk % kAStages, pa = (kk / kAStages) & 1u;
             const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-            if (!mbar_wait(&sh->a_full[st], ph, sh, status) || !mbar_wait(&sh->b_full[st], ph, sh, status)) {
+            if (!mbar_wait(&sh->a_full[sa], pa, sh, status) || !mbar_wait(&sh->b_full[st], ph, sh, status)) {
               alive = false;
               break;
             }
             fence_after();
-            const uint32_t a_hi = tmem + kAccCols + st * 64, a_lo = a_hi + 32;
+            const uint32_t a_hi = tmem + kAccCols + sa * 64, a_lo = a_hi + 32;
             const uint32_t b_hi = smem_u32(bstage + st * kStageBytes), b_lo = b_hi + kBBytes;
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks) {
@@ -606,7 +615,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
                 mma_ts(tmem, a_lo + ks * 8, sdesc_sw128(b_hi + ks * 32), idesc, 1);
               }
             }
-            mma_commit(&sh->empty[st]);
+            mma_commit(&sh->empty[sa]);
             if (g.cs > 1)
               mma_commit_mc(&sh->bempty[st], cmask);
             else

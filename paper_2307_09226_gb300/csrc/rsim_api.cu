@@ -92,6 +92,8 @@ rsim_status check_params(const rsim_radar_params* p, Consts* k) {
   k->k_da = p->mu * d / (c * p->fs);
   k->k_g = d / p->lambda;
   k->k_b = -2.0 * ts / p->lambda;
+  if (p->flags & ~RSIM_FLAG_TDM_MOTION) return fail(RSIM_ERR_INVALID_ARG, "unknown flag bits");
+  k->k_m = (p->flags & RSIM_FLAG_TDM_MOTION) ? -2.0 * p->t_b / p->lambda : 0.0;
   return RSIM_OK;
 }
 

@@ -20,9 +20,11 @@ constexpr int kMaxSplits = 64;
 //   a_{p,v} = k_a0 R_p + v k_da u_p    (2 mu R_{p,v} / (c F_s), cycles per sample)
 //   c_{p,v} = v k_g u_p                (v d_rx u_p / lambda, cycles)
 //   b_p     = k_b vel_p                (-2 vel_p T_slow / lambda, cycles per block)
+// and, with RSIM_FLAG_TDM_MOTION, c_{p,v} gains m k_m vel_p (-2 vel_p m T_b / lambda,
+// Tx slot m = v / N); k_m = 0 otherwise.
 struct Consts {
   int M, N, V, Ns, L;
-  double k_a0, k_da, k_g, k_b;
+  double k_a0, k_da, k_g, k_b, k_m;
 };
 
 // One frame as the kernels see it: caller buffers plus this frame's workspace slices.

@@ -43,6 +43,7 @@ class Radar:
     t_b: float = 60e-6  # chirp duration [s]
     t_slow: float = 0.0  # TDM block period [s]; <= 0 means M * t_b
     c: float = C_LIGHT
+    tdm_motion: bool = False  # add the Doppler phase of the Tx slot within a block
 
     @property
     def V(self) -> int:

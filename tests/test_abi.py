@@ -42,15 +42,16 @@ def test_version_and_last_error_are_host_only(lib):
 
 
 def test_struct_layouts_match_header():
-    # rsim_radar_params: 4 int32 + 7 double
-    assert ctypes.sizeof(_abi.rsim_radar_params) == 16 + 7 * 8
+    # rsim_radar_params: 4 int32 + 7 double + flags + reserved
+    assert ctypes.sizeof(_abi.rsim_radar_params) == 16 + 7 * 8 + 8
+    assert _abi.rsim_radar_params.flags.offset == 72
     assert _abi.rsim_radar_params.lambda_.offset == 16
     # rsim_pixels: int64 + 2 int32 + 6 pointers
     assert ctypes.sizeof(_abi.rsim_pixels) == 16 + 6 * 8
     assert _abi.rsim_pixels.range.offset == 16
     assert ctypes.sizeof(_abi.rsim_plan) == 32
     assert ctypes.sizeof(_abi.rsim_server_opts) == 16
-    assert ctypes.sizeof(_abi.rsim_request) == 72 + 64 + 8 + 8
+    assert ctypes.sizeof(_abi.rsim_request) == 80 + 64 + 8 + 8
     assert ctypes.sizeof(_abi.rsim_server_stats) == 4 * 8 + 6 * 8 + 8 + 8
 
 
