@@ -204,6 +204,24 @@ rsim_status rsim_path_phases(rsim_ctx* ctx, const rsim_radar_params* params,
                              const rsim_pixels* pixels, uint32_t* a, uint32_t* cph, uint32_t* b,
                              float* sigma, int64_t* p_valid, rsim_stream stream);
 
+/* Target estimation on complex64 cubes (Section III: an FFT of each CPI's cube gives
+ * the range-Doppler map; the velocity of maximum power per CPI gives the Doppler-time
+ * plot).  For each of the F cubes (HOST array of device pointers, laid out as in
+ * rsim_synth with these params, complex64):
+ *   power[f][k][d] = sum over channels v of |sum_n sum_l cube[v][n][l]
+ *                    e^{-j 2 pi (k n / N_s + d l / L)}|^2          (DEVICE, float)
+ *   v_est[f]       = velocity [m/s] of the Doppler bin of the largest power[f][k][d]
+ *                    (first index on ties), v = -d_s lambda / (2 T_slow L) with d_s the
+ *                    signed bin in [-L/2, L/2)                       (DEVICE, float)
+ *   peak[2f], peak[2f+1] = (k, d) of that maximum (DEVICE int32, may be NULL).
+ * options: RSIM_RD_SKIP_STATIC leaves the zero-Doppler column out of the search (a
+ * static-clutter notch).  N_s and L must be powers of two up to 1024 (else UNSUPPORTED).
+ * Uses the context workspace.  Asynchronous on `stream`. */
+#define RSIM_RD_SKIP_STATIC 1
+rsim_status rsim_range_doppler(rsim_ctx* ctx, const rsim_radar_params* params, void* const* cubes,
+                               int32_t F, float* power, float* v_est, int32_t* peak, int32_t options,
+                               rsim_stream stream);
+
 /* Wait for `stream`, then return (and clear) the context's device-side status:
  * RSIM_OK, RSIM_ERR_NONFINITE or RSIM_ERR_TIMEOUT. */
 rsim_status rsim_sync_status(rsim_ctx* ctx, rsim_stream stream);

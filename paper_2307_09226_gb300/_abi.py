@@ -89,6 +89,8 @@ SIGNATURES = {
     "rsim_valid_indices": (c_int, [c_void_p, POINTER(rsim_pixels), c_void_p, c_void_p, c_void_p]),
     "rsim_path_phases": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels),
                                  c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "rsim_range_doppler": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(c_void_p), c_int32,
+                                   c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "rsim_sync_status": (c_int, [c_void_p, c_void_p]),
     "rsim_autotune": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
                               POINTER(rsim_plan), c_void_p]),
@@ -237,6 +239,19 @@ def rsim_path_phases(ctx, radar, pixels, a, cph, b, sigma, p_valid, stream=None)
     px = pixels if isinstance(pixels, rsim_pixels) else pixels_struct(pixels)
     check(load().rsim_path_phases(ctx, ctypes.byref(radar_params(radar)), ctypes.byref(px), _ptr(a),
                                   _ptr(cph), _ptr(b), _ptr(sigma), _ptr(p_valid), _stream(stream)))
+
+
+RD_SKIP_STATIC = 1
+
+
+def rsim_range_doppler(ctx, radar, cubes, power, v_est, peak=None, skip_static=False, stream=None):
+    """cubes: list of complex64 device tensors [V, Ns, L]; power: float32 [F, Ns, L];
+    v_est: float32 [F]; peak: int32 [F, 2] or None."""
+    F = len(cubes)
+    ptrs = (c_void_p * F)(*[c.data_ptr() for c in cubes])
+    check(load().rsim_range_doppler(ctx, ctypes.byref(radar_params(radar)), ptrs, F, _ptr(power),
+                                    _ptr(v_est), _ptr(peak), RD_SKIP_STATIC if skip_static else 0,
+                                    _stream(stream)))
 
 
 def rsim_sync_status(ctx, stream=None) -> int:

@@ -80,6 +80,10 @@ cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int split
                         int out_dtype, int grid, int cluster, bool use_partial, int num_sms,
                         int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st);
 
+cudaError_t launch_range_doppler(const float2* const* cubes_dev, float2* tmp, float* power, int F,
+                                 int V, int Ns, int L, int skip_static, double v_per_bin, float* v_est,
+                                 int32_t* peak, cudaStream_t st);
+
 // Plan rule shared by single-frame and batch paths (depends on the shape only).
 int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms);
 int units_per_split(int tier, int V, int Ns, int L);

@@ -259,3 +259,31 @@ def test_tdm_motion_term_turns_tx_slots_by_the_doppler_of_one_chirp():
                                    rtol=1e-10, atol=1e-10)
     np.testing.assert_allclose(plain[4], plain[0], rtol=1e-12)
     assert oracle.rel_l2(oracle.cube_separable(replace(radar, tdm_motion=True), px), tdm) < 1e-12
+
+
+def test_range_doppler_peak_recovers_range_and_velocity():
+    """A point target on integer bins: the range-Doppler peak sits at the FMCW range bin
+    and the Doppler bin, and the max-power velocity is the target's velocity."""
+    radar = Radar(M=2, N=4, Ns=64, L=32)
+    r = radar.resolved()
+    k_r, k_d = 9, 5
+    R = k_r * r.c * r.fs / (2 * r.mu * r.Ns)
+    for sign in (1, -1):
+        vel = sign * k_d * r.lam / (2 * r.t_slow * r.L)
+        cube = oracle.cube_literal(radar, _one(radar, R, 1 + 0j, 0.0, 0.0, vel))
+        pw = oracle.range_doppler_power(cube)
+        v, (k, d) = oracle.max_power_velocity(radar, pw)
+        assert (k, d) == (k_r, (-sign * k_d) % r.L)
+        assert abs(v - vel) < 1e-12
+        # all the energy of V unit channels is in that bin: V * (N_s L)^2
+        assert abs(pw[k, d] - r.V * (r.Ns * r.L) ** 2) < 1e-6 * pw[k, d]
+    # a static reflector dominates unless the zero-Doppler column is notched out
+    cube = oracle.cube_literal(radar, _one(radar, R, 3 + 0j, 0.0, 0.0, 0.0)) + \
+        oracle.cube_literal(radar, _one(radar, R, 1 + 0j, 0.0, 0.0, vel))
+    pw = oracle.range_doppler_power(cube)
+    assert oracle.max_power_velocity(radar, pw)[1][1] == 0
+    assert abs(oracle.max_power_velocity(radar, pw, skip_static=True)[0] - vel) < 1e-12
+
+
+def test_e_velo_is_the_mean_absolute_error():
+    assert oracle.e_velo([1.0, -2.0, 0.5], [1.5, -1.0, 0.5]) == pytest.approx(0.5)
