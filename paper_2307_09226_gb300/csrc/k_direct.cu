@@ -16,7 +16,7 @@
 namespace rsim {
 namespace {
 
-constexpr int kTN = 64;       // n per tile
+constexpr int kTN = 128;      // n per tile
 constexpr int kTL = 64;       // l per tile
 constexpr int kThreads = 256;
 
@@ -37,7 +37,42 @@ __device__ __forceinline__ void cmac(float2& acc, float2 g, float2 d) {
   acc.y = fmaf(g.y, d.x, acc.y);
 }
 
-__global__ void __launch_bounds__(kThreads)
+// Phasor tiles of one 32-pixel chunk: G[q][n] = e^{j 2 pi (a n + c)} (channel v),
+// D[q][l] = sigma e^{j 2 pi b l}; zero outside the frame / the cube.
+__device__ __forceinline__ void fill_chunk(float2 (*Gs)[kTN], float2 (*Ds)[kTL], const FrameIO& fr,
+                                           const uint32_t* pA, const uint32_t* pC, int64_t q0,
+                                           int64_t pv, int n0, int l0, const Consts& k) {
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int i = 0; i < (kChunkPx * kTN) / kThreads; ++i) {
+    const int e = tid + i * kThreads;
+    const int qq = e / kTN, nn = e % kTN;
+    const int64_t q = q0 + qq;
+    const int n = n0 + nn;
+    float2 g = make_float2(0.f, 0.f);
+    if (q < pv && n < k.Ns) g = cis_q32(pA[q] * (uint32_t)n + pC[q]);
+    Gs[qq][nn] = g;
+  }
+#pragma unroll
+  for (int i = 0; i < (kChunkPx * kTL) / kThreads; ++i) {
+    const int e = tid + i * kThreads;
+    const int qq = e / kTL, ll = e % kTL;
+    const int64_t q = q0 + qq;
+    const int l = l0 + ll;
+    float2 d = make_float2(0.f, 0.f);
+    if (q < pv && l < k.L) {
+      const float2 w = cis_q32(fr.phB[q] * (uint32_t)l);
+      const float2 sg = fr.sig[q];
+      d = make_float2(sg.x * w.x - sg.y * w.y, sg.x * w.y + sg.y * w.x);
+    }
+    Ds[qq][ll] = d;
+  }
+}
+
+// One CTA: a 128 (n) x 64 (l) tile of one channel over one pixel split.  Each thread
+// owns 8 n x 4 l complex outputs; the phasor tiles are double-buffered so that the next
+// chunk is filled before the barrier that hands it over.
+__global__ void __launch_bounds__(kThreads, 2)
 direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_per_frame,
            int out_dtype) {
   const int f = blockIdx.x / units_per_frame;
@@ -57,69 +92,53 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
   const int64_t nch = (pv + kChunkPx - 1) / kChunkPx;
   const int64_t c0 = nch * s / splits, c1 = nch * (s + 1) / splits;
 
-  __shared__ float2 Gs[kChunkPx][kTN];
-  __shared__ float2 Ds[kChunkPx][kTL];
+  extern __shared__ float2 dsm[];  // 2 x (G [32][128] + D [32][64])
+  constexpr int kBuf = kChunkPx * (kTN + kTL);
+  auto gbuf = [&](int b) { return reinterpret_cast<float2 (*)[kTN]>(dsm + b * kBuf); };
+  auto dbuf = [&](int b) { return reinterpret_cast<float2 (*)[kTL]>(dsm + b * kBuf + kChunkPx * kTN); };
 
   const int tid = threadIdx.x;
-  const int tn = tid >> 4, tl = tid & 15;  // rows tn*4 .. +3 ; cols tl + 16 j
-  float2 acc[4][4];
+  const int tn = tid >> 4, tl = tid & 15;  // rows tn*8 .. +7 ; cols tl + 16 j
+  float2 acc[8][4];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < 8; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
   const uint32_t* pA = fr.phA + (int64_t)v * fr.Pcap;
   const uint32_t* pC = fr.phC + (int64_t)v * fr.Pcap;
 
+  if (c0 < c1) fill_chunk(gbuf(0), dbuf(0), fr, pA, pC, c0 * kChunkPx, pv, n0, l0, k);
+  __syncthreads();
   for (int64_t c = c0; c < c1; ++c) {
-    const int64_t q0 = c * kChunkPx;
-    __syncthreads();
-#pragma unroll
-    for (int i = 0; i < (kChunkPx * kTN) / kThreads; ++i) {
-      const int e = tid + i * kThreads;
-      const int qq = e / kTN, nn = e % kTN;
-      const int64_t q = q0 + qq;
-      const int n = n0 + nn;
-      float2 g = make_float2(0.f, 0.f);
-      if (q < pv && n < k.Ns) g = cis_q32(pA[q] * (uint32_t)n + pC[q]);
-      Gs[qq][nn] = g;
-    }
-#pragma unroll
-    for (int i = 0; i < (kChunkPx * kTL) / kThreads; ++i) {
-      const int e = tid + i * kThreads;
-      const int qq = e / kTL, ll = e % kTL;
-      const int64_t q = q0 + qq;
-      const int l = l0 + ll;
-      float2 d = make_float2(0.f, 0.f);
-      if (q < pv && l < k.L) {
-        const float2 w = cis_q32(fr.phB[q] * (uint32_t)l);
-        const float2 sg = fr.sig[q];
-        d = make_float2(sg.x * w.x - sg.y * w.y, sg.x * w.y + sg.y * w.x);
-      }
-      Ds[qq][ll] = d;
-    }
-    __syncthreads();
-#pragma unroll 4
+    const int b = (int)((c - c0) & 1);
+    if (c + 1 < c1) fill_chunk(gbuf(b ^ 1), dbuf(b ^ 1), fr, pA, pC, (c + 1) * kChunkPx, pv, n0, l0, k);
+    const float2 (*G)[kTN] = gbuf(b);
+    const float2 (*D)[kTL] = dbuf(b);
+#pragma unroll 2
     for (int qq = 0; qq < kChunkPx; ++qq) {
-      const float4 ga = *reinterpret_cast<const float4*>(&Gs[qq][tn * 4]);
-      const float4 gb = *reinterpret_cast<const float4*>(&Gs[qq][tn * 4 + 2]);
-      const float2 g[4] = {make_float2(ga.x, ga.y), make_float2(ga.z, ga.w),
-                           make_float2(gb.x, gb.y), make_float2(gb.z, gb.w)};
-      float2 d[4];
+      float2 g[8], d[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) d[j] = Ds[qq][tl + 16 * j];
+      for (int i = 0; i < 8; i += 2) {
+        const float4 t = *reinterpret_cast<const float4*>(&G[qq][tn * 8 + i]);
+        g[i] = make_float2(t.x, t.y);
+        g[i + 1] = make_float2(t.z, t.w);
+      }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int j = 0; j < 4; ++j) d[j] = D[qq][tl + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) cmac(acc[i][j], g[i], d[j]);
     }
+    __syncthreads();
   }
 
   // write the tile: final cube when there is one split, else this split's partial
   const int64_t rows = (int64_t)k.V * k.Ns;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int n = n0 + tn * 4 + i;
+  for (int i = 0; i < 8; ++i) {
+    const int n = n0 + tn * 8 + i;
     if (n >= k.Ns) continue;
     const int64_t row = (int64_t)v * k.Ns + n;
 #pragma unroll
@@ -194,7 +213,10 @@ cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int spl
   const int64_t blocks = upf * F;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-  direct_sum<<<(unsigned)blocks, kThreads, 0, st>>>(frames, k, splits, (int)upf, out_dtype);
+  const int smem = (int)sizeof(float2) * 2 * kChunkPx * (kTN + kTL);
+  cudaError_t e = cudaFuncSetAttribute(direct_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  direct_sum<<<(unsigned)blocks, kThreads, smem, st>>>(frames, k, splits, (int)upf, out_dtype);
   return cudaGetLastError();
 }
 
@@ -234,15 +256,24 @@ int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms) {
   int64_t smax = chunks / 8 > 0 ? chunks / 8 : 1;
   if (smax > kMaxSplits) smax = kMaxSplits;
   if (tier == RSIM_TIER_FP32) {
-    // about 4 resident CTAs per SM
-    int64_t s = (4ll * num_sms + tiles - 1) / tiles;
-    if (s > smax) s = smax;
     // FP32 accumulation: at most 8192 pixels per split, so that the running sum of
     // random-phase terms keeps a relative rounding error of a few 1e-6 (the splits are
-    // then added in FP64)
-    s = std::max<int64_t>(s, (P + 8191) / 8192);
-    if (s > kMaxSplits) s = kMaxSplits;
-    return (int)std::max<int64_t>(s, 1);
+    // then added with compensated sums); above that, the split count that fills whole
+    // waves of two resident CTAs per SM best
+    const int64_t smin = std::min<int64_t>(std::max<int64_t>((P + 8191) / 8192, 1), kMaxSplits);
+    const int64_t slots = 2ll * num_sms;
+    double best = -1.0;
+    int64_t bs = smin;
+    for (int64_t s = smin; s <= std::max(smin, smax); ++s) {
+      const int64_t units = (int64_t)tiles * s;
+      const int64_t waves = (units + slots - 1) / slots;
+      const double eff = (double)units / (double)(waves * slots) - 0.001 * s;
+      if (eff > best + 1e-9) {
+        best = eff;
+        bs = s;
+      }
+    }
+    return (int)bs;
   }
   // tensor tiers: one persistent CTA per SM takes equal units from a counter; pick the
   // split count whose unit count fills whole rounds of SMs best, with a small cost per

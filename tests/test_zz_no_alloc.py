@@ -29,7 +29,7 @@ def env():
 
 
 @pytest.mark.parametrize("tier,maker", [
-    ("fp32", synth.config2),
+    ("fp32", lambda: synth.parity_frame(seed=40, M=2, N=4, Ns=128, L=64, n_az=128, n_el=128)),
     ("split_fp16", lambda: synth.parity_frame(seed=41, M=3, N=4, Ns=128, L=64, n_az=90, n_el=80)),
     ("split_bf16", lambda: synth.parity_frame(seed=42, M=2, N=3, Ns=96, L=48, n_az=71, n_el=70)),
 ])
