@@ -124,6 +124,12 @@ __device__ __noinline__ bool mbar_wait(uint64_t* b, uint32_t parity, Shared* sh,
   }
 }
 
+// Inline fast path of mbar_wait for the MMA thread: one probe of a phase that has
+// usually completed already, the bounded polling loop only when it has not.
+__device__ __forceinline__ bool mbar_wait_fast(uint64_t* b, uint32_t parity, Shared* sh, unsigned* status) {
+  return mbar_try(b, parity) || mbar_wait(b, parity, sh, status);
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
   asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
                    smem_u32(b)),
@@ -195,12 +201,53 @@ __host__ __device__ constexpr uint32_t idesc_f16(int bf16, int n) {
          ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
-                                       uint32_t accum) {
+// All MMAs of one 32-pixel operand stage (K = 64 16-bit elements = four K = 16 steps),
+// in one block so that nothing is recomputed between issues.  `a`: tensor-memory column
+// of the stage's hi A part (the lo part starts 32 columns on); `bd`: shared-memory
+// descriptor of the stage's hi B image (the lo image starts kBBytes on).  K step ks
+// reads A columns a + 8 ks and B bytes + 32 ks (2 in the descriptor's 16-byte address
+// field).  Split tiers add A_hi B_lo and A_lo B_hi after each A_hi B_hi.  `acc` = 0
+// starts a new accumulation with the stage's first MMA.
+template <int SPLIT>
+__device__ __forceinline__ void mma_stage(uint32_t d, uint32_t a, uint64_t bd, uint32_t idesc, uint32_t acc);
+
+template <>
+__device__ __forceinline__ void mma_stage<0>(uint32_t d, uint32_t a, uint64_t bd, uint32_t idesc, uint32_t acc) {
   asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
-      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accum)
+      "{\n\t.reg .pred p, t;\n\t"
+      "setp.ne.b32 p, %10, 0;\n\t"
+      "setp.ne.b32 t, %9, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %5, %9, p;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], %6, %9, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%3], %7, %9, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%4], %8, %9, t;\n\t}" ::"r"(d),
+      "r"(a), "r"(a + 8), "r"(a + 16), "r"(a + 24), "l"(bd), "l"(bd + 2), "l"(bd + 4), "l"(bd + 6),
+      "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+template <>
+__device__ __forceinline__ void mma_stage<1>(uint32_t d, uint32_t a, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  constexpr uint64_t kLo = kBBytes >> 4;
+  asm volatile(
+      "{\n\t.reg .pred p, t;\n\t"
+      "setp.ne.b32 p, %18, 0;\n\t"
+      "setp.ne.b32 t, %17, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %9, %17, p;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %13, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%5], %9, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], %10, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%2], %14, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%6], %10, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%3], %11, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%3], %15, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%7], %11, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%4], %12, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%4], %16, %17, t;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%8], %12, %17, t;\n\t}" ::"r"(d),
+      "r"(a), "r"(a + 8), "r"(a + 16), "r"(a + 24), "r"(a + 32), "r"(a + 40), "r"(a + 48), "r"(a + 56),
+      "l"(bd), "l"(bd + 2), "l"(bd + 4), "l"(bd + 6), "l"(bd + kLo), "l"(bd + kLo + 2), "l"(bd + kLo + 4),
+      "l"(bd + kLo + 6), "r"(idesc), "r"(acc)
       : "memory");
 }
 
@@ -585,6 +632,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
       uint32_t kk = 0, gi = 0, ui = 0;
       long long u;
       bool alive = true;
+      const uint64_t desc0 = sdesc_sw128(smem_u32(bstage));  // hi image of B stage 0
       while (alive && next_unit(sh, ui++, status, &u, false)) {
         const Unit x = decode(g, frames, k, u, rank);
         int64_t g0 = x.c0;
@@ -599,22 +647,15 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           for (int64_t c = g0; c < g1; ++c, ++kk) {
             const uint32_t sa = kk % kAStages, pa = (kk / kAStages) & 1u;
             const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-            if (!mbar_wait(&sh->a_full[sa], pa, sh, status) || !mbar_wait(&sh->b_full[st], ph, sh, status)) {
+            if (!mbar_wait_fast(&sh->a_full[sa], pa, sh, status) ||
+                !mbar_wait_fast(&sh->b_full[st], ph, sh, status)) {
               alive = false;
               break;
             }
             fence_after();
-            const uint32_t a_hi = tmem + kAccCols + sa * 64, a_lo = a_hi + 32;
-            const uint32_t b_hi = smem_u32(bstage + st * kStageBytes), b_lo = b_hi + kBBytes;
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks) {
-              mma_ts(tmem, a_hi + ks * 8, sdesc_sw128(b_hi + ks * 32), idesc, accum);
-              accum = 1;
-              if (SPLIT) {
-                mma_ts(tmem, a_hi + ks * 8, sdesc_sw128(b_lo + ks * 32), idesc, 1);
-                mma_ts(tmem, a_lo + ks * 8, sdesc_sw128(b_hi + ks * 32), idesc, 1);
-              }
-            }
+            mma_stage<SPLIT>(tmem, tmem + kAccCols + sa * 64, desc0 + (uint64_t)(st * (kStageBytes >> 4)),
+                             idesc, accum);
+            accum = 1;
             mma_commit(&sh->empty[sa]);
             if (g.cs > 1)
               mma_commit_mc(&sh->bempty[st], cmask);
