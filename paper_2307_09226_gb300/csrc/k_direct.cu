@@ -158,15 +158,6 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
   }
 }
 
-// Add x to the compensated sum (s, c) (Kahan): the running error of FP32 additions is
-// carried in c, so the sum of a few dozen partials is as accurate as one rounding.
-__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
-  const float y = x - c;
-  const float t = s + y;
-  c = (t - s) - y;
-  s = t;
-}
-
 // cube = scale * sum over splits s = 0, 1, ... (in this order) of partial[s], with
 // compensated FP32 additions (GB300's FP64 rate is a small fraction of its FP32 rate).
 // Loads of eight splits are issued together; the additions keep the split order.

@@ -324,6 +324,7 @@ struct Geo {
   int cs;                // CTAs per cluster: consecutive row tiles sharing one B stream
   int mgroups;           // groups of cs row tiles
   int64_t total_units;   // cluster work units (frame, row-tile group, column tile, split)
+  int64_t sstride;       // complex elements of one split's tiled partial sums
   const int32_t* order;  // frames by decreasing valid-pixel count
 };
 
@@ -577,18 +578,14 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
             for (int i = 0; i < 8; ++i) re[i] = im[i] = 0u;
           }
           if (!row_ok) continue;
-          float2* dst = g.direct ? nullptr : fr.partial + (int64_t)x.s * rows_total * k.L + gr * k.L;
-          // later groups are added with reductions: no load round trip, and one thread
-          // owns each address, so its additions land in program order (deterministic)
-          const bool vec = (k.L % 2 == 0);
+          if (g.direct) {
 #pragma unroll
-          for (int i = 0; i < 8; i += 2) {
-            const int l = l0 + jb + i;
-            if (l >= k.L) break;
-            const float a0 = __uint_as_float(re[i]), b0 = __uint_as_float(im[i]);
-            const float a1 = __uint_as_float(re[i + 1]), b1 = __uint_as_float(im[i + 1]);
-            const bool two = (l + 1 < k.L);
-            if (g.direct) {
+            for (int i = 0; i < 8; i += 2) {
+              const int l = l0 + jb + i;
+              if (l >= k.L) break;
+              const float a0 = __uint_as_float(re[i]), b0 = __uint_as_float(im[i]);
+              const float a1 = __uint_as_float(re[i + 1]), b1 = __uint_as_float(im[i + 1]);
+              const bool two = (l + 1 < k.L);
               const int64_t o = gr * k.L + l;
               if (out_dtype == RSIM_C128) {
                 double2* cd = reinterpret_cast<double2*>(fr.cube);
@@ -599,24 +596,24 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
                 cf[o] = make_float2(a0 * oscale, b0 * oscale);
                 if (two) cf[o + 1] = make_float2(a1 * oscale, b1 * oscale);
               }
-            } else if (vec && two) {
-              float4* d4 = reinterpret_cast<float4*>(dst + l);
-              const float4 v4 = make_float4(a0, b0, a1, b1);
+            }
+          } else {
+            // tiled partial sums: column pair p of accumulator row r is float4 p * 128 + r of
+            // the tile, so the warp's 32 rows write 512 contiguous bytes.  Later groups are
+            // added with reductions: no load round trip, and one thread owns each address, so
+            // its additions land in program order (deterministic).  Columns past L (last
+            // column tile) land in the tile's padding and are never read.
+            float4* t4 = reinterpret_cast<float4*>(fr.partial + (int64_t)x.s * g.sstride +
+                                                   ((int64_t)x.mt * g.ntiles + x.nt) * (128 * g.NT)) +
+                         (jb >> 1) * 128 + r;
+#pragma unroll
+            for (int i = 0; i < 8; i += 2) {
+              const float4 v4 = make_float4(__uint_as_float(re[i]), __uint_as_float(im[i]),
+                                            __uint_as_float(re[i + 1]), __uint_as_float(im[i + 1]));
               if (first)
-                *d4 = v4;
+                t4[(i >> 1) * 128] = v4;
               else
-                atomicAdd(d4, v4);
-            } else {
-              if (first)
-                dst[l] = make_float2(a0, b0);
-              else
-                atomicAdd(dst + l, make_float2(a0, b0));
-              if (two) {
-                if (first)
-                  dst[l + 1] = make_float2(a1, b1);
-                else
-                  atomicAdd(dst + l + 1, make_float2(a1, b1));
-              }
+                atomicAdd(t4 + (i >> 1) * 128, v4);
             }
           }
         }
@@ -756,6 +753,60 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   }
 }
 
+// cube = scale * sum over splits s = 0, 1, ... (in this order) of the tiled partial
+// sums, with compensated FP32 additions per component.  One thread per (accumulator
+// row, column pair) of a tile: the loads of consecutive threads are contiguous.  Eight
+// splits' loads are issued together; the additions keep the split order.
+__global__ void split_reduce_tiles(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles,
+                                   int64_t sstride, int splits, int out_dtype, int scale_mode) {
+  const FrameIO& fr = frames[blockIdx.y];
+  float scale = 1.f;
+  if (scale_mode) {
+    const float m = __uint_as_float((unsigned)fr.meta[1]);
+    scale = (m > 0.f) ? ldexpf(1.f, ilogbf(m) + 1) : 1.f;
+  }
+  const int64_t rows = (int64_t)k.V * k.Ns;
+  const int64_t n4 = sstride / 2;
+  const int pairs = NT / 2;
+  const float4* __restrict__ part = reinterpret_cast<const float4*>(fr.partial);
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e & 127);
+    const int64_t q = e >> 7;
+    const int pr = (int)(q % pairs);
+    const int64_t tile = q / pairs;
+    const int64_t row = (tile / ntiles) * 128 + r;
+    const int l = (int)(tile % ntiles) * NT + 2 * pr;
+    if (row >= rows || l >= k.L) continue;
+    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
+    for (int b = 0; b < splits; b += 8) {
+      float4 p[8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        p[j] = (b + j < splits) ? __ldcs(part + (int64_t)(b + j) * n4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        if (b + j < splits) {
+          kahan_add(s0, c0, p[j].x);
+          kahan_add(s1, c1, p[j].y);
+          kahan_add(s2, c2, p[j].z);
+          kahan_add(s3, c3, p[j].w);
+        }
+      }
+    }
+    const int64_t o = row * k.L + l;
+    const bool two = (l + 1 < k.L);
+    if (out_dtype == RSIM_C128) {
+      double2* cd = reinterpret_cast<double2*>(fr.cube);
+      cd[o] = make_double2((double)(s0 * scale), (double)(s1 * scale));
+      if (two) cd[o + 1] = make_double2((double)(s2 * scale), (double)(s3 * scale));
+    } else {
+      float2* cf = reinterpret_cast<float2*>(fr.cube);
+      cf[o] = make_float2(s0 * scale, s1 * scale);
+      if (two) cf[o + 1] = make_float2(s2 * scale, s3 * scale);
+    }
+  }
+}
+
 // Frames by decreasing valid-pixel count (ties by index): the persistent kernel takes
 // the units of the largest frames first.
 __global__ void order_frames(const FrameIO* __restrict__ frames, int F, int32_t* order) {
@@ -819,6 +870,25 @@ cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, in
 
 int tile_nt(int L) { return L >= 128 ? 128 : ((L + 7) / 8) * 8; }
 
+int64_t tensor_split_stride(int V, int Ns, int L) {
+  const int nt = tile_nt(L);
+  const int64_t mtiles = ((int64_t)V * Ns + 127) / 128;
+  return mtiles * ((L + nt - 1) / nt) * 128 * nt;
+}
+
+cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
+                                bool scale_from_meta, cudaStream_t st) {
+  const int nt = tile_nt(k.L);
+  const int64_t sstride = tensor_split_stride(k.V, k.Ns, k.L);
+  const int64_t n4 = sstride / 2;
+  if (n4 <= 0 || F <= 0) return cudaSuccess;
+  int64_t blocks = (n4 + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  split_reduce_tiles<<<dim3((unsigned)blocks, F), 256, 0, st>>>(frames, k, nt, (k.L + nt - 1) / nt, sstride,
+                                                                splits, out_dtype, scale_from_meta ? 1 : 0);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
                         int out_dtype, int grid, int cluster, bool use_partial, int num_sms,
                         int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st) {
@@ -834,6 +904,7 @@ cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int split
   g.upf = g.mgroups * g.ntiles * splits;
   g.group = group_chunks(tier);
   g.direct = use_partial ? 0 : 1;
+  g.sstride = tensor_split_stride(k.V, k.Ns, k.L);
   g.F = F;
   g.total_units = (int64_t)g.upf * F;
   if (g.total_units <= 0) return cudaSuccess;

@@ -53,7 +53,10 @@ FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_p
   fl.blk = o;      o = align_up(o + 4 * (size_t)((P + kPrepTile - 1) / kPrepTile + 1), 256);
   fl.meta = 0;     // lives in the batch header
   fl.partial = o;
-  if (use_partial) o = align_up(o + 8 * (size_t)splits * V * Ns * L, 256);
+  if (use_partial) {
+    const int64_t per_split = tensor ? tensor_split_stride(V, Ns, L) : (int64_t)V * Ns * L;
+    o = align_up(o + 8 * (size_t)splits * per_split, 256);
+  }
   // slow-time operand images: [column tile][chunk][hi, lo][2 NT rows x 128 B]
   fl.bimg_nch = Pcap / kChunkPx;
   fl.bimg = align_up(o, 1024);
@@ -278,7 +281,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     if (prof) cudaEventRecord(ev[2], st);
     if (use_partial) {
       const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
-      e = launch_reduce(k, table, F, splits, out_dtype, scaled ? 1.f : 0.f, st);
+      e = launch_reduce_tiles(k, table, F, splits, out_dtype, scaled, st);
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
     }
   }

@@ -45,7 +45,8 @@ struct FrameIO {
   float2* sig;                // [Pcap]    sigma (FP32)
   int32_t* blk_count;         // [ceil(P / kPrepTile)] valid pixels per prep block
   unsigned long long* meta;   // [0] P_valid, [1] max(|re|,|im|) of sigma as float bits
-  float2* partial;            // [splits][V*Ns][L] split partial sums (NULL if splits == 1)
+  float2* partial;            // split partial sums (NULL when unused): FP32 tier [splits][V*Ns][L];
+                              // tensor tiers in tiles, see tensor_split_stride
   unsigned char* bimg;        // tensor tiers: slow-time operand as shared-memory images
   int64_t bimg_nch;           // chunk capacity of bimg per column tile
   int32_t splits;             // pixel splits of the contraction
@@ -65,6 +66,19 @@ FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_p
 // Columns of l per tensor-core column tile, and the bytes of one 16-bit part of one
 // chunk's slow-time operand image (2 NT rows of 128 B).
 int tile_nt(int L);
+// Complex elements of one split's partial sums on the tensor tiers.  They are stored
+// by accumulator tile, [row tile][column tile][column pair][128 rows][2 columns], so
+// that a warp's 32 accumulator rows drain into 512 contiguous bytes.
+int64_t tensor_split_stride(int V, int Ns, int L);
+
+// Add x to the compensated sum (s, c) (Kahan): the running error of FP32 additions is
+// carried in c, so the sum of a few dozen partials is as accurate as one rounding.
+__device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
+  const float y = x - c;
+  const float t = s + y;
+  c = (t - s) - y;
+  s = t;
+}
 inline size_t bimg_part_bytes(int L) { return (size_t)2 * tile_nt(L) * 128; }
 
 // Launches (all asynchronous on `st`).  `frames` is a device array of F FrameIO.
@@ -74,6 +88,9 @@ cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int spl
                           int out_dtype, cudaStream_t st);
 cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
                           float scale_from_meta, cudaStream_t st);
+// The same reduction over the tensor tiers' tiled partial sums.
+cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
+                                bool scale_from_meta, cudaStream_t st);
 // cluster: CTAs per thread-block cluster that share the slow-time operand by
 // multicast (1, 2, 4 or 8).
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
