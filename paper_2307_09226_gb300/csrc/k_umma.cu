@@ -18,16 +18,20 @@
 // reused, so it is generated on chip and never touches HBM.
 //
 // The contraction runs one persistent CTA per SM, warp-specialised:
-//   warps 0-7  produce A for a 128-row tile straight into tensor memory (one row per
-//              thread, two warps per lane quarter, 16 pixels each, tcgen05.st), and
-//              drain the accumulator (tcgen05.ld) after each group of chunks;
-//   warp 8     allocates tensor memory and one thread issues tcgen05.mma
-//              (M = 128, N = 2 NT, K = 16, A from tensor memory, B from shared memory);
-//   warp 9     takes work units from a device counter and bulk-copies each chunk's
-//              phases of the tile's channels into a shared-memory ring;
-//   warp 10    bulk-copies each chunk's B images into the operand stages.
-// Stages are handed over with mbarriers; every wait is bounded in time and a timeout
-// sets a status bit instead of hanging.
+//   warps 0-15  produce A for a 128-row tile straight into tensor memory (one row per
+//               thread, tcgen05.st).  Two groups of 8 warps take alternate stages; in a
+//               stage, two warps share a lane quarter with 16 pixels each.  The same
+//               warps drain the accumulator (tcgen05.ld) after each group of chunks;
+//   warp 16     allocates tensor memory and one thread issues tcgen05.mma
+//               (M = 128, N = 2 NT, K = 16, A from tensor memory, B from shared memory);
+//   warp 17     takes work units from a device counter and bulk-copies each chunk's
+//               phases of the tile's channels into a shared-memory ring;
+//   warp 18     bulk-copies each chunk's B images into the operand stages.
+// An operand stage (A in tensor memory, B in shared memory) has one "full" mbarrier,
+// completed by the producer group's arrivals and the B copy's bytes, and one "empty"
+// mbarrier, completed by a tcgen05.commit after the stage's MMAs: the MMA thread waits
+// once and commits once per stage.  Every wait is bounded in time and a timeout sets a
+// status bit instead of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -36,8 +40,7 @@
 namespace rsim {
 namespace {
 
-constexpr int kAStages = 4;                // A stages in tensor memory (64 columns each)
-constexpr int kStages = 3;                 // B stages in shared memory (64 KB each)
+constexpr int kStages = 3;                 // operand stages: A in tensor memory (64 columns), B in shared memory (64 KB)
 constexpr int kPixStages = 6;              // ring of staged per-chunk pixel phases
 constexpr int kUnitSlots = 4;              // ring of work-unit ids
 constexpr int kMaxCh = 8;                  // channels a row tile may span for staging
@@ -59,10 +62,9 @@ struct PixStage {
 };
 
 struct Shared {
-  uint64_t a_full[kAStages];
-  uint64_t empty[kAStages];  // this CTA's MMAs are done with the A stage (it may be rewritten)
-  uint64_t b_full[kStages];
-  uint64_t bempty[kStages];  // every CTA of the cluster is done with the B stage
+  uint64_t full[kStages];    // the stage's A (producer arrivals) and B (bulk-copy bytes) are in place
+  uint64_t empty[kStages];   // this CTA's MMAs are done with the stage (it may be rewritten)
+  uint64_t bempty[kStages];  // clusters: every CTA of the cluster is done with the B stage
   uint64_t pix_full[kPixStages];
   uint64_t pix_empty[kPixStages];
   uint64_t unit_full[kUnitSlots];
@@ -457,12 +459,9 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   const uint16_t cmask = (uint16_t)((1u << g.cs) - 1u);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < kAStages; ++i) {
-      mbar_init(&sh->a_full[i], 32 * kAGroupWarps);
-      mbar_init(&sh->empty[i], 1);
-    }
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&sh->b_full[i], 1);
+      mbar_init(&sh->full[i], 32 * kAGroupWarps + 1);  // one producer group + the B loader
+      mbar_init(&sh->empty[i], 1);
       mbar_init(&sh->bempty[i], g.cs);
     }
     for (int i = 0; i < kPixStages; ++i) {
@@ -521,7 +520,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         const int64_t g1 = (x.c1 < g0 + g.group) ? x.c1 : g0 + g.group;
         for (int64_t c = g0; c < g1; ++c, ++kk, ++pk) {
           if ((int)(kk & 1u) != group) continue;  // the other group makes this stage
-          const uint32_t st = kk % kAStages, ph = (kk / kAStages) & 1u;
+          const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
           const uint32_t ps = pk % kPixStages, pph = (pk / kPixStages) & 1u;
           if (!warp_wait(&sh->pix_full[ps], pph, sh, status) ||
               !warp_wait(&sh->empty[st], ph ^ 1u, sh, status)) {
@@ -557,7 +556,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           if (SPLIT) tmem_st16(col + 32, lo);
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           fence_before();
-          mbar_arrive(&sh->a_full[st]);
+          mbar_arrive(&sh->full[st]);
         }
         if (!alive) break;
         // ---- drain this group's accumulator (round-to-nearest FP32 adds) ----
@@ -642,22 +641,17 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           fence_after();
           uint32_t accum = 0;
           for (int64_t c = g0; c < g1; ++c, ++kk) {
-            const uint32_t sa = kk % kAStages, pa = (kk / kAStages) & 1u;
             const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-            if (!mbar_wait_fast(&sh->a_full[sa], pa, sh, status) ||
-                !mbar_wait_fast(&sh->b_full[st], ph, sh, status)) {
+            if (!mbar_wait_fast(&sh->full[st], ph, sh, status)) {
               alive = false;
               break;
             }
             fence_after();
-            mma_stage<SPLIT>(tmem, tmem + kAccCols + sa * 64, desc0 + (uint64_t)(st * (kStageBytes >> 4)),
+            mma_stage<SPLIT>(tmem, tmem + kAccCols + st * 64, desc0 + (uint64_t)(st * (kStageBytes >> 4)),
                              idesc, accum);
             accum = 1;
-            mma_commit(&sh->empty[sa]);
-            if (g.cs > 1)
-              mma_commit_mc(&sh->bempty[st], cmask);
-            else
-              mma_commit(&sh->bempty[st]);
+            mma_commit(&sh->empty[st]);
+            if (g.cs > 1) mma_commit_mc(&sh->bempty[st], cmask);
           }
           if (!alive) break;
           if (g1 > g0)
@@ -723,20 +717,20 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         const FrameIO& fr = frames[x.f];
         for (int64_t c = x.c0; c < x.c1; ++c, ++kk) {
           const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-          if (!mbar_wait(&sh->bempty[st], ph ^ 1u, sh, status)) {
+          if (!mbar_wait(g.cs > 1 ? &sh->bempty[st] : &sh->empty[st], ph ^ 1u, sh, status)) {
             alive = false;
             break;
           }
           const unsigned char* src = fr.bimg + ((int64_t)x.nt * fr.bimg_nch + c) * 2 * part;
           unsigned char* dst = bstage + st * kStageBytes;
-          mbar_expect_tx(&sh->b_full[st], SPLIT ? 2 * part : part);
+          mbar_expect_tx(&sh->full[st], SPLIT ? 2 * part : part);
           if (g.cs > 1) {
             const uint32_t slice = part / g.cs, off = slice * rank;
-            bulk_g2s_mc(dst + off, src + off, slice, &sh->b_full[st], cmask);
-            if (SPLIT) bulk_g2s_mc(dst + kBBytes + off, src + part + off, slice, &sh->b_full[st], cmask);
+            bulk_g2s_mc(dst + off, src + off, slice, &sh->full[st], cmask);
+            if (SPLIT) bulk_g2s_mc(dst + kBBytes + off, src + part + off, slice, &sh->full[st], cmask);
           } else {
-            bulk_g2s(dst, src, part, &sh->b_full[st]);
-            if (SPLIT) bulk_g2s(dst + kBBytes, src + part, part, &sh->b_full[st]);
+            bulk_g2s(dst, src, part, &sh->full[st]);
+            if (SPLIT) bulk_g2s(dst + kBBytes, src + part, part, &sh->full[st]);
           }
         }
       }
