@@ -26,11 +26,27 @@ __device__ __forceinline__ bool is_valid(const T* sre, const T* sim, int64_t p) 
   return (sre[p] != T(0)) || (sim[p] != T(0));
 }
 
-// frac(x) as an unsigned 64-bit fixed-point number of 2^-64 units, rounded to nearest.
+// frac(x) = x - floor(x) as an unsigned 64-bit fixed-point number of 2^-64 units, read
+// from the binary representation with integer operations (GB300's FP64 rate is a small
+// fraction of its integer rate).  x = m 2^(E - 1075) with the 53-bit significand m, so
+// frac(x) 2^64 = m 2^(E - 1011) mod 2^64: exact when that shift is >= 0, else rounded to
+// the nearest unit (half up).  A negative x gives 2^64 - frac(|x|) 2^64 (mod 2^64).
 __device__ __forceinline__ uint64_t frac_u64(double x) {
-  double f = x - floor(x);  // exact for |x| < 2^52; in [0, 1]
-  if (!(f < 1.0)) f = 0.0;  // x = -tiny can give f == 1.0
-  return __double2ull_rn(f * 18446744073709551616.0);
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (E == 0 || E == 0x7FF) return 0;  // zero, subnormal (< 2^-1022) or not finite
+  const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - 1011;
+  uint64_t f;
+  if (sh >= 64)
+    f = 0;  // x is a multiple of 2^64 units: an integer
+  else if (sh >= 0)
+    f = m << sh;
+  else if (sh >= -53)
+    f = (m >> -sh) + ((m >> (-sh - 1)) & 1ull);
+  else
+    f = 0;  // below half a unit
+  return (bits >> 63) ? (uint64_t)0 - f : f;
 }
 
 // Round a 2^-64 fixed-point fraction to the nearest 2^-32 unit (mod 1).

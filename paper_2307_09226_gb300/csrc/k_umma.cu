@@ -339,7 +339,7 @@ struct Unit {
 __device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, const Consts& k,
                                        int64_t u, int rank) {
   Unit x;
-  x.f = g.order[u / g.upf];
+  x.f = g.order ? g.order[u / g.upf] : (int)(u / g.upf);
   // row-tile group fastest: the CTAs running at the same time share a pixel range and
   // so the same slow-time operand images in L2
   int r = (int)(u % g.upf);
@@ -398,46 +398,54 @@ __device__ __forceinline__ bool next_unit(Shared* sh, uint32_t ui, unsigned* sta
 // ---------------------------------------------------------------------------------
 template <int BF, int SPLIT>
 __global__ void __launch_bounds__(256)
-build_b_images(const FrameIO* __restrict__ frames, Consts k, int NT, int scaled) {
-  const FrameIO& fr = frames[blockIdx.z];
-  const int64_t c = blockIdx.x;
-  const int nt = blockIdx.y;
-  const int64_t pv = (int64_t)fr.meta[0];
-  if (c * kChunkPx >= pv) return;
-  const float sc = sigma_scale(fr, scaled);
+build_b_images(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles, int64_t nch, int F,
+               int scaled) {
   const size_t part = (size_t)2 * NT * 128;
-  unsigned char* base = fr.bimg + ((int64_t)nt * fr.bimg_nch + c) * 2 * part;
-  const int64_t q0c = c * kChunkPx;
-  for (int e = threadIdx.x; e < 2 * NT * 8; e += blockDim.x) {
-    const int row = e >> 3, cp = e & 7;
-    const int qg = cp ^ (row & 7);
-    const bool imrow = row >= NT;
-    const int l = nt * NT + (imrow ? row - NT : row);
-    const int64_t q0 = q0c + qg * 4;
-    const uint4 b4 = *reinterpret_cast<const uint4*>(fr.phB + q0);
-    const float4 s01 = *reinterpret_cast<const float4*>(fr.sig + q0);
-    const float4 s23 = *reinterpret_cast<const float4*>(fr.sig + q0 + 2);
-    const uint32_t bv[4] = {b4.x, b4.y, b4.z, b4.w};
-    const float sr[4] = {s01.x, s01.z, s23.x, s23.z};
-    const float si[4] = {s01.y, s01.w, s23.y, s23.w};
-    uint32_t hi[4], lo[4];
+  const int64_t items = (int64_t)F * ntiles * nch;
+  // one chunk image per block and pass, chunks of a column tile consecutive
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t c = it % nch;
+    const int nt = (int)((it / nch) % ntiles);
+    const FrameIO& fr = frames[it / (nch * ntiles)];
+    const int64_t pv = (int64_t)fr.meta[0];
+    if (c * kChunkPx >= pv) continue;
+    const float sc = sigma_scale(fr, scaled);
+    unsigned char* base = fr.bimg + ((int64_t)nt * fr.bimg_nch + c) * 2 * part;
+    const int64_t q0c = c * kChunkPx;
+    // element (l, 16-byte column cp): four pixels' D at l, written to the re-row l and
+    // the im-row NT + l, which share a swizzle pattern (NT is a multiple of 8)
+    for (int e = threadIdx.x; e < NT * 8; e += blockDim.x) {
+      const int row = e >> 3, cp = e & 7;
+      const int qg = cp ^ (row & 7);
+      const int l = nt * NT + row;
+      const int64_t q0 = q0c + qg * 4;
+      const uint4 b4 = *reinterpret_cast<const uint4*>(fr.phB + q0);
+      const float4 s01 = *reinterpret_cast<const float4*>(fr.sig + q0);
+      const float4 s23 = *reinterpret_cast<const float4*>(fr.sig + q0 + 2);
+      const uint32_t bv[4] = {b4.x, b4.y, b4.z, b4.w};
+      const float sr[4] = {s01.x, s01.z, s23.x, s23.z};
+      const float si[4] = {s01.y, s01.w, s23.y, s23.w};
+      uint32_t rhi[4], rlo[4], ihi[4], ilo[4];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float dre = 0.f, dim = 0.f;
-      if (l < k.L && q0 + i < pv) {
-        const float2 w = cis_q32(bv[i] * (uint32_t)l);
-        const float a = sr[i] * sc, b = si[i] * sc;
-        dre = a * w.x - b * w.y;
-        dim = a * w.y + b * w.x;
+      for (int i = 0; i < 4; ++i) {
+        float dre = 0.f, dim = 0.f;
+        if (l < k.L && q0 + i < pv) {
+          const float2 w = cis_q32(bv[i] * (uint32_t)l);
+          const float a = sr[i] * sc, b = si[i] * sc;
+          dre = a * w.x - b * w.y;
+          dim = a * w.y + b * w.x;
+        }
+        split2<BF>(dre, -dim, rhi[i], rlo[i]);
+        split2<BF>(dim, dre, ihi[i], ilo[i]);
       }
-      if (imrow)
-        split2<BF>(dim, dre, hi[i], lo[i]);
-      else
-        split2<BF>(dre, -dim, hi[i], lo[i]);
+      const size_t off = (size_t)row * 128 + cp * 16, ioff = off + (size_t)NT * 128;
+      *reinterpret_cast<uint4*>(base + off) = make_uint4(rhi[0], rhi[1], rhi[2], rhi[3]);
+      *reinterpret_cast<uint4*>(base + ioff) = make_uint4(ihi[0], ihi[1], ihi[2], ihi[3]);
+      if (SPLIT) {
+        *reinterpret_cast<uint4*>(base + part + off) = make_uint4(rlo[0], rlo[1], rlo[2], rlo[3]);
+        *reinterpret_cast<uint4*>(base + part + ioff) = make_uint4(ilo[0], ilo[1], ilo[2], ilo[3]);
+      }
     }
-    const size_t off = (size_t)row * 128 + cp * 16;
-    *reinterpret_cast<uint4*>(base + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-    if (SPLIT) *reinterpret_cast<uint4*>(base + part + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
   }
 }
 
@@ -820,7 +828,10 @@ cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, in
                      int out_dtype, int64_t nch_max, unsigned* status, int* counter, cudaStream_t st) {
   cudaError_t e;
   if (nch_max > 0) {
-    build_b_images<BF, SPLIT><<<dim3((unsigned)nch_max, g.ntiles, g.F), 256, 0, st>>>(frames, k, g.NT, scaled);
+    // one wave of resident blocks (8 x 256 threads per SM), looping over the chunk images
+    const int64_t items = (int64_t)g.F * g.ntiles * nch_max;
+    const int blocks = (int)std::min<int64_t>(items, 8ll * num_sms);
+    build_b_images<BF, SPLIT><<<blocks, 256, 0, st>>>(frames, k, g.NT, g.ntiles, nch_max, g.F, scaled);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -871,13 +882,15 @@ int64_t tensor_split_stride(int V, int Ns, int L) {
 }
 
 cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
-                                bool scale_from_meta, cudaStream_t st) {
+                                bool scale_from_meta, int num_sms, cudaStream_t st) {
   const int nt = tile_nt(k.L);
   const int64_t sstride = tensor_split_stride(k.V, k.Ns, k.L);
   const int64_t n4 = sstride / 2;
   if (n4 <= 0 || F <= 0) return cudaSuccess;
+  // one wave of resident blocks (8 x 256 threads per SM) over all frames, grid-stride
   int64_t blocks = (n4 + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
+  const int64_t wave = std::max<int64_t>(1, 8ll * num_sms / F);
+  if (blocks > wave) blocks = wave;
   split_reduce_tiles<<<dim3((unsigned)blocks, F), 256, 0, st>>>(frames, k, nt, (k.L + nt - 1) / nt, sstride,
                                                                 splits, out_dtype, scale_from_meta ? 1 : 0);
   return cudaGetLastError();
@@ -904,10 +917,14 @@ cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int split
   if (g.total_units <= 0) return cudaSuccess;
   // the unit counter (int) and the frame order (F ints) share the counter region
   int32_t* order = unit_counter + 4;
-  g.order = order;
-  order_frames<<<1, 256, 0, st>>>(frames, F, order);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  g.order = nullptr;
+  cudaError_t e = cudaSuccess;
+  if (F > 1) {  // one frame needs no ordering
+    g.order = order;
+    order_frames<<<1, 256, 0, st>>>(frames, F, order);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   const int64_t nch_max = (max_p + kChunkPx - 1) / kChunkPx;
   switch (tier) {
     case RSIM_TIER_BF16:

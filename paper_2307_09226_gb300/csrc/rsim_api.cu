@@ -281,7 +281,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     if (prof) cudaEventRecord(ev[2], st);
     if (use_partial) {
       const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
-      e = launch_reduce_tiles(k, table, F, splits, out_dtype, scaled, st);
+      e = launch_reduce_tiles(k, table, F, splits, out_dtype, scaled, ctx->num_sms, st);
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
     }
   }

@@ -90,7 +90,7 @@ cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int spl
                           float scale_from_meta, cudaStream_t st);
 // The same reduction over the tensor tiers' tiled partial sums.
 cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
-                                bool scale_from_meta, cudaStream_t st);
+                                bool scale_from_meta, int num_sms, cudaStream_t st);
 // cluster: CTAs per thread-block cluster that share the slow-time operand by
 // multicast (1, 2, 4 or 8).
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,

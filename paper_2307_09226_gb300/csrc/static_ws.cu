@@ -137,7 +137,7 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
-    if (use_partial) e = launch_reduce_tiles(k, table, 1, splits, out_dtype, scaled, st);
+    if (use_partial) e = launch_reduce_tiles(k, table, 1, splits, out_dtype, scaled, sms, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "split reduction");
   return RSIM_OK;
