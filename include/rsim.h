@@ -228,15 +228,19 @@ rsim_status rsim_sync_status(rsim_ctx* ctx, rsim_stream stream);
 
 /* Stage timing for benchmarks.  While profiling is on, every rsim_synth /
  * rsim_synth_batch call records CUDA events on its stream around its three stages
- * (compaction + FP64 phases, contraction, split reduction).  rsim_profile_read waits
- * for the recorded events, returns the summed stage times and launch counts since
- * profiling was switched on, and starts a new tally. */
+ * (compaction + FP64 phases, contraction, split reduction), and on the tensor-core
+ * tiers between the operand-builder kernel and the contraction kernel.  The events
+ * stand between the stages' kernels, so profiled calls do not overlap one stage's
+ * launch with the previous stage's end.  rsim_profile_read waits for the recorded
+ * events, returns the summed stage times and launch counts since profiling was
+ * switched on, and starts a new tally. */
 typedef struct {
   int32_t calls;            /* synth calls recorded */
   int32_t kernels;          /* kernels those calls launched */
   double prep_ms;           /* summed device time of the compaction + phase kernels */
   double contract_ms;       /* summed device time of the contraction kernel */
   double reduce_ms;         /* summed device time of the split reduction (0 if none) */
+  double operand_ms;        /* part of contract_ms spent in the operand builder (tensor tiers) */
 } rsim_profile;
 
 rsim_status rsim_profile_enable(rsim_ctx* ctx, int32_t on);

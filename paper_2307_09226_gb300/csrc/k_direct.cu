@@ -75,6 +75,7 @@ __device__ __forceinline__ void fill_chunk(float2 (*Gs)[kTN], float2 (*Ds)[kTL],
 __global__ void __launch_bounds__(kThreads, 2)
 direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_per_frame,
            int out_dtype) {
+  wait_prior_grid();
   const int f = blockIdx.x / units_per_frame;
   int r = blockIdx.x % units_per_frame;
   const FrameIO& fr = frames[f];
@@ -163,6 +164,7 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
 // Loads of eight splits are issued together; the additions keep the split order.
 __global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, int splits,
                              int out_dtype, int scale_mode) {
+  wait_prior_grid();
   const FrameIO& fr = frames[blockIdx.y];
   float scale = 1.f;
   if (scale_mode) {
@@ -207,8 +209,8 @@ cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int spl
   const int smem = (int)sizeof(float2) * 2 * kChunkPx * (kTN + kTL);
   cudaError_t e = cudaFuncSetAttribute(direct_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  direct_sum<<<(unsigned)blocks, kThreads, smem, st>>>(frames, k, splits, (int)upf, out_dtype);
-  return cudaGetLastError();
+  return launch_dependent(direct_sum, dim3((unsigned)blocks), dim3(kThreads), (size_t)smem, st, frames, k, splits,
+                          (int)upf, out_dtype);
 }
 
 cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
@@ -218,8 +220,8 @@ cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int spl
   int64_t blocks = (count + 255) / 256;
   if (blocks > 4096) blocks = 4096;
   dim3 grid((unsigned)blocks, F);
-  split_reduce<<<grid, 256, 0, st>>>(frames, count, splits, out_dtype, scale_mode != 0.f ? 1 : 0);
-  return cudaGetLastError();
+  return launch_dependent(split_reduce, grid, dim3(256), 0, st, frames, count, splits, out_dtype,
+                          scale_mode != 0.f ? 1 : 0);
 }
 
 bool uses_partial(int tier, int64_t P, int splits) {

@@ -16,6 +16,8 @@
 // Both are deterministic (no atomics decide positions).
 #include <math.h>
 
+#include <algorithm>
+
 #include "rsim_internal.h"
 
 namespace rsim {
@@ -54,9 +56,20 @@ __device__ __forceinline__ uint32_t top32(uint64_t x) {
   return (uint32_t)((x + 0x80000000ull) >> 32);
 }
 
+// `one`: with use_one, the (single) frame's entry, passed by value and stored to
+// frames[0] here, so that no host-to-device copy precedes the kernels.  Block 0 of each
+// frame clears its meta words and block (0, 0) the work-unit counter of the contraction.
 template <typename T>
-__global__ void __launch_bounds__(kPrepThreads) prep_count(const FrameIO* __restrict__ frames) {
-  const FrameIO& fr = frames[blockIdx.y];
+__global__ void __launch_bounds__(kPrepThreads)
+prep_count(FrameIO* __restrict__ frames, FrameIO one, int use_one, int* counter) {
+  const FrameIO fr = use_one ? one : frames[blockIdx.y];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (use_one) frames[0] = one;
+    fr.meta[0] = 0ull;  // valid-pixel count, written by prep_scatter
+    fr.meta[1] = 0ull;  // max |sigma| accumulator, filled by prep_scatter
+    if (counter && blockIdx.y == 0)
+      for (int i = 0; i < 4; ++i) counter[i] = 0;
+  }
   const int64_t base = (int64_t)blockIdx.x * kPrepTile;
   if (base >= fr.P) return;
   const T* sre = (const T*)fr.sre;
@@ -75,13 +88,13 @@ __global__ void __launch_bounds__(kPrepThreads) prep_count(const FrameIO* __rest
     int s = 0;
     for (int w = 0; w < kPrepThreads / 32; ++w) s += ws[w];
     fr.blk_count[blockIdx.x] = s;
-    if (blockIdx.x == 0) fr.meta[1] = 0ull;  // max |sigma| accumulator, filled by prep_scatter
   }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kPrepThreads)
 prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigned* status) {
+  wait_prior_grid();
   const FrameIO& fr = frames[blockIdx.y];
   const int64_t base = (int64_t)blockIdx.x * kPrepTile;
   if (base >= fr.P) return;
@@ -177,17 +190,23 @@ prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigne
 
 }  // namespace
 
-cudaError_t launch_prep(const Consts& k, const FrameIO* frames, int F, int64_t maxP, int dtype,
-                        bool idx_only, unsigned* status, cudaStream_t st) {
-  if (F <= 0 || maxP <= 0) return cudaSuccess;
-  const int nblk = (int)((maxP + kPrepTile - 1) / kPrepTile);
+cudaError_t launch_prep(const Consts& k, FrameIO* frames, const FrameIO* one, int F, int64_t maxP,
+                        int dtype, bool idx_only, unsigned* status, int* counter, cudaStream_t st) {
+  if (F <= 0) return cudaSuccess;
+  const int nblk = (int)std::max<int64_t>(1, (maxP + kPrepTile - 1) / kPrepTile);
   dim3 grid(nblk, F);
+  const FrameIO arg = one ? *one : FrameIO{};
+  const int use_one = one ? 1 : 0;
   if (dtype == RSIM_F64) {
-    prep_count<double><<<grid, kPrepThreads, 0, st>>>(frames);
-    prep_scatter<double><<<grid, kPrepThreads, 0, st>>>(frames, k, idx_only ? 1 : 0, status);
+    prep_count<double><<<grid, kPrepThreads, 0, st>>>(frames, arg, use_one, counter);
+    if (maxP > 0)
+      return launch_dependent(prep_scatter<double>, grid, dim3(kPrepThreads), 0, st, (const FrameIO*)frames, k,
+                              idx_only ? 1 : 0, status);
   } else {
-    prep_count<float><<<grid, kPrepThreads, 0, st>>>(frames);
-    prep_scatter<float><<<grid, kPrepThreads, 0, st>>>(frames, k, idx_only ? 1 : 0, status);
+    prep_count<float><<<grid, kPrepThreads, 0, st>>>(frames, arg, use_one, counter);
+    if (maxP > 0)
+      return launch_dependent(prep_scatter<float>, grid, dim3(kPrepThreads), 0, st, (const FrameIO*)frames, k,
+                              idx_only ? 1 : 0, status);
   }
   return cudaGetLastError();
 }

@@ -400,6 +400,7 @@ template <int BF, int SPLIT>
 __global__ void __launch_bounds__(256)
 build_b_images(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles, int64_t nch, int F,
                int scaled) {
+  wait_prior_grid();
   const size_t part = (size_t)2 * NT * 128;
   const int64_t items = (int64_t)F * ntiles * nch;
   // one chunk image per block and pass, chunks of a column tile consecutive
@@ -497,6 +498,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   __syncthreads();
   fence_after();
   if (g.cs > 1) cluster_sync();  // peers' barriers are initialised before any multicast
+  wait_prior_grid();  // the set-up above overlaps the operand builder's last blocks
   const uint32_t tmem = sh->tmem_base;
   const int64_t rows_total = (int64_t)k.V * k.Ns;
 
@@ -761,6 +763,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
 // splits' loads are issued together; the additions keep the split order.
 __global__ void split_reduce_tiles(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles,
                                    int64_t sstride, int splits, int out_dtype, int scale_mode) {
+  wait_prior_grid();
   const FrameIO& fr = frames[blockIdx.y];
   float scale = 1.f;
   if (scale_mode) {
@@ -825,33 +828,38 @@ __global__ void order_frames(const FrameIO* __restrict__ frames, int F, int32_t*
 
 template <int BF, int SPLIT>
 cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, int num_sms, int scaled,
-                     int out_dtype, int64_t nch_max, unsigned* status, int* counter, cudaStream_t st) {
+                     int out_dtype, int64_t nch_max, unsigned* status, int* counter, cudaStream_t st,
+                     cudaEvent_t mid) {
   cudaError_t e;
   if (nch_max > 0) {
     // one wave of resident blocks (8 x 256 threads per SM), looping over the chunk images
     const int64_t items = (int64_t)g.F * g.ntiles * nch_max;
     const int blocks = (int)std::min<int64_t>(items, 8ll * num_sms);
-    build_b_images<BF, SPLIT><<<blocks, 256, 0, st>>>(frames, k, g.NT, g.ntiles, nch_max, g.F, scaled);
-    e = cudaGetLastError();
+    e = launch_dependent(build_b_images<BF, SPLIT>, dim3(blocks), dim3(256), 0, st, frames, k, g.NT, g.ntiles,
+                         nch_max, g.F, scaled);
     if (e != cudaSuccess) return e;
   }
+  if (mid) cudaEventRecord(mid, st);
   const int smem = kStages * kStageBytes + kPixStages * (int)sizeof(PixStage) + (int)sizeof(Shared) + 1024;
   auto fn = umma_contract<BF, SPLIT>;
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   int clusters;
   if (g.cs > 1) {
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = g.cs;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    attr[1].id = cudaLaunchAttributeClusterDimension;
+    attr[1].val.clusterDim.x = g.cs;
+    attr[1].val.clusterDim.y = 1;
+    attr[1].val.clusterDim.z = 1;
+    cfg.numAttrs = 2;
     // the schedule is static per cluster, so launch only clusters that fit at once
     cfg.gridDim = dim3(g.cs * (num_sms / g.cs));
     int fit = 0;
@@ -891,14 +899,14 @@ cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, i
   int64_t blocks = (n4 + 255) / 256;
   const int64_t wave = std::max<int64_t>(1, 8ll * num_sms / F);
   if (blocks > wave) blocks = wave;
-  split_reduce_tiles<<<dim3((unsigned)blocks, F), 256, 0, st>>>(frames, k, nt, (k.L + nt - 1) / nt, sstride,
-                                                                splits, out_dtype, scale_from_meta ? 1 : 0);
-  return cudaGetLastError();
+  return launch_dependent(split_reduce_tiles, dim3((unsigned)blocks, F), dim3(256), 0, st, frames, k, nt,
+                          (k.L + nt - 1) / nt, sstride, splits, out_dtype, scale_from_meta ? 1 : 0);
 }
 
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
                         int out_dtype, int grid, int cluster, bool use_partial, int num_sms,
-                        int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st) {
+                        int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st,
+                        cudaEvent_t mid) {
   Geo g;
   const int64_t rows = (int64_t)k.V * k.Ns;
   g.NT = tile_nt(k.L);
@@ -914,7 +922,10 @@ cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int split
   g.sstride = tensor_split_stride(k.V, k.Ns, k.L);
   g.F = F;
   g.total_units = (int64_t)g.upf * F;
-  if (g.total_units <= 0) return cudaSuccess;
+  if (g.total_units <= 0) {
+    if (mid) cudaEventRecord(mid, st);
+    return cudaSuccess;
+  }
   // the unit counter (int) and the frame order (F ints) share the counter region
   int32_t* order = unit_counter + 4;
   g.order = nullptr;
@@ -928,13 +939,13 @@ cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int split
   const int64_t nch_max = (max_p + kChunkPx - 1) / kChunkPx;
   switch (tier) {
     case RSIM_TIER_BF16:
-      return launch_t<1, 0>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, status, unit_counter, st);
+      return launch_t<1, 0>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, status, unit_counter, st, mid);
     case RSIM_TIER_SPLIT_BF16:
-      return launch_t<1, 1>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, status, unit_counter, st);
+      return launch_t<1, 1>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, status, unit_counter, st, mid);
     case RSIM_TIER_SPLIT_FP16:
-      return launch_t<0, 1>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, status, unit_counter, st);
+      return launch_t<0, 1>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, status, unit_counter, st, mid);
     case RSIM_TIER_FP16:
-      return launch_t<0, 0>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, status, unit_counter, st);
+      return launch_t<0, 0>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, status, unit_counter, st, mid);
     default:
       return cudaErrorInvalidValue;
   }

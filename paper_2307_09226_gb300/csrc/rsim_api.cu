@@ -174,7 +174,9 @@ rsim_status ensure_workspace(rsim_ctx* ctx, size_t bytes, cudaStream_t st) {
   return RSIM_OK;
 }
 
-// Fill FrameIO entries for F frames in workspace `ws` and upload the table.
+// Fill FrameIO entries for F frames in workspace `ws`.  A batch's table is uploaded
+// here; a single frame's entry goes to the first kernel by value (launch_prep), and the
+// meta words and the unit counter are cleared by that kernel too.
 rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pixels* frames,
                          int F, void* const* cubes, int splits, bool use_partial, bool tensor,
                          cudaStream_t st, std::vector<FrameIO>& host, FrameIO** dev_table,
@@ -212,11 +214,11 @@ rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pi
     io.splits = splits;
   }
   *dev_table = (FrameIO*)ws;
-  cudaError_t e = cudaMemcpyAsync(ws, host.data(), sizeof(FrameIO) * (size_t)F,
-                                  cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
-  e = cudaMemsetAsync(meta, 0, 16 * (size_t)F, st);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(meta)");
+  if (F > 1) {
+    cudaError_t e = cudaMemcpyAsync(ws, host.data(), sizeof(FrameIO) * (size_t)F,
+                                    cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
+  }
   return RSIM_OK;
 }
 
@@ -244,26 +246,32 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
                                tier != RSIM_TIER_FP32, st, host, &table, &counter);
   if (s != RSIM_OK) return s;
   // stage events when profiling this context's own calls
-  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // ev: start, after compaction + phases, after the contraction, after the reduction,
+  // and (tensor tiers) between the operand builder and the contraction kernel
+  cudaEvent_t ev[kProfEvents] = {};
   const bool prof = ctx->prof && status == ctx->status_dev;
   if (prof) {
-    const size_t base = 4 * (size_t)ctx->prof_calls;
-    while (ctx->ev_pool.size() < base + 4) {
+    const size_t base = kProfEvents * (size_t)ctx->prof_calls;
+    while (ctx->ev_pool.size() < base + kProfEvents) {
       cudaEvent_t x;
       if (cudaEventCreate(&x) != cudaSuccess) return cuda_fail(cudaGetLastError(), "cudaEventCreate");
       ctx->ev_pool.push_back(x);
     }
-    for (int i = 0; i < 4; ++i) ev[i] = ctx->ev_pool[base + i];
+    for (int i = 0; i < kProfEvents; ++i) ev[i] = ctx->ev_pool[base + i];
     ctx->prof_calls++;
-    // compaction + phases (2), contraction (1, plus the frame-order kernel on tensor tiers),
-    // split reduction (1 when the partial buffer is used)
-    ctx->prof_kernels += 3 + (tier != RSIM_TIER_FP32 ? 1 : 0) + (use_partial ? 1 : 0);
+    // compaction + phases (2); FP32: direct sum (1); tensor tiers: operand builder (1 when
+    // a frame has valid pixels), frame order (1 for a batch), contraction (1); the split
+    // reduction (1 when the partial buffer is used)
+    const bool tensor = tier != RSIM_TIER_FP32;
+    ctx->prof_kernels += 2 + (tensor ? 1 + (mp > 0 ? 1 : 0) + (F > 1 ? 1 : 0) : 1) + (use_partial ? 1 : 0);
     cudaEventRecord(ev[0], st);
   }
-  cudaError_t e = launch_prep(k, table, F, mp, frames[0].dtype, false, status, st);
+  cudaError_t e = launch_prep(k, table, F == 1 ? host.data() : nullptr, F, mp, frames[0].dtype, false, status,
+                              counter, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (prof) cudaEventRecord(ev[1], st);
   if (tier == RSIM_TIER_FP32) {
+    if (prof) cudaEventRecord(ev[4], st);
     e = launch_direct(k, table, F, splits, out_dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
     if (prof) cudaEventRecord(ev[2], st);
@@ -272,10 +280,8 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
     }
   } else {
-    e = cudaMemsetAsync(counter, 0, 16, st);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counter)");
     e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, plan_cluster(plan), use_partial,
-                    ctx->num_sms, mp, status, counter, st);
+                    ctx->num_sms, mp, status, counter, st, prof ? ev[4] : nullptr);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     if (prof) cudaEventRecord(ev[2], st);
@@ -421,7 +427,7 @@ rsim_status rsim_valid_indices(rsim_ctx* ctx, const rsim_pixels* pixels, int32_t
   host[0].idx = idx;
   cudaError_t e = cudaMemcpyAsync(table, host.data(), sizeof(FrameIO), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
-  e = launch_prep(k, table, 1, P, pixels->dtype, true, ctx->status_dev, st);
+  e = launch_prep(k, table, host.data(), 1, P, pixels->dtype, true, ctx->status_dev, nullptr, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   e = cudaMemcpyAsync(p_valid, host[0].meta, 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "copy of the valid count");
@@ -456,7 +462,7 @@ rsim_status rsim_path_phases(rsim_ctx* ctx, const rsim_radar_params* params,
   host[0].Pcap = P;
   cudaError_t e = cudaMemcpyAsync(table, host.data(), sizeof(FrameIO), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
-  e = launch_prep(k, table, 1, P, pixels->dtype, false, ctx->status_dev, st);
+  e = launch_prep(k, table, host.data(), 1, P, pixels->dtype, false, ctx->status_dev, nullptr, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   e = cudaMemcpyAsync(p_valid, host[0].meta, 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "copy of the valid count");
@@ -493,16 +499,18 @@ rsim_status rsim_profile_read(rsim_ctx* ctx, rsim_profile* out) {
   p.calls = ctx->prof_calls;
   p.kernels = ctx->prof_kernels;
   for (int c = 0; c < ctx->prof_calls; ++c) {
-    cudaEvent_t* ev = &ctx->ev_pool[4 * (size_t)c];
+    cudaEvent_t* ev = &ctx->ev_pool[kProfEvents * (size_t)c];
     cudaError_t e = cudaEventSynchronize(ev[3]);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-    float a = 0, b = 0, d = 0;
+    float a = 0, b = 0, d = 0, o = 0;
     cudaEventElapsedTime(&a, ev[0], ev[1]);
     cudaEventElapsedTime(&b, ev[1], ev[2]);
     cudaEventElapsedTime(&d, ev[2], ev[3]);
+    cudaEventElapsedTime(&o, ev[1], ev[4]);
     p.prep_ms += a;
     p.contract_ms += b;
     p.reduce_ms += d;
+    p.operand_ms += o;
   }
   ctx->prof_calls = 0;
   ctx->prof_kernels = 0;

@@ -9,6 +9,9 @@
 
 #include "rsim_internal.h"
 
+// CUDA events a profiled synth call records (stage boundaries).
+constexpr int kProfEvents = 5;
+
 struct rsim_ctx {
   int device = 0;
   int num_sms = 0;
@@ -21,7 +24,7 @@ struct rsim_ctx {
   std::map<std::string, rsim_plan> plans;
   // stage profiling (rsim_profile_enable / rsim_profile_read)
   bool prof = false;
-  std::vector<cudaEvent_t> ev_pool;  // 4 events per recorded call
+  std::vector<cudaEvent_t> ev_pool;  // kProfEvents events per recorded call
   int prof_calls = 0;
   int prof_kernels = 0;
 };

@@ -71,6 +71,30 @@ int tile_nt(int L);
 // that a warp's 32 accumulator rows drain into 512 contiguous bytes.
 int64_t tensor_split_stride(int V, int Ns, int L);
 
+// Programmatic dependent launch: a kernel launched with launch_dependent may be
+// scheduled while the previous kernel in the stream drains its last blocks, hiding the
+// launch latency between the stages of one call.  Such a kernel executes
+// wait_prior_grid() before it touches anything the previous kernel writes; the wait
+// returns once that kernel has completed and its writes are visible (it is a no-op for
+// a kernel launched without the attribute).
+__device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                             Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 // Add x to the compensated sum (s, c) (Kahan): the running error of FP32 additions is
 // carried in c, so the sum of a few dozen partials is as accurate as one rounding.
 __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
@@ -82,8 +106,11 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
 inline size_t bimg_part_bytes(int L) { return (size_t)2 * tile_nt(L) * 128; }
 
 // Launches (all asynchronous on `st`).  `frames` is a device array of F FrameIO.
-cudaError_t launch_prep(const Consts& k, const FrameIO* frames, int F, int64_t maxP, int dtype,
-                        bool write_idx_only, unsigned* status, cudaStream_t st);
+// Compaction and phases.  `one` (F == 1 only, else NULL): the frame's entry, which the
+// first kernel stores to frames[0] (no upload needed); the kernels also clear each
+// frame's meta words and, when `counter` is given, the contraction's work-unit counter.
+cudaError_t launch_prep(const Consts& k, FrameIO* frames, const FrameIO* one, int F, int64_t maxP,
+                        int dtype, bool write_idx_only, unsigned* status, int* counter, cudaStream_t st);
 cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits,
                           int out_dtype, cudaStream_t st);
 cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
@@ -92,10 +119,12 @@ cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int spl
 cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
                                 bool scale_from_meta, int num_sms, cudaStream_t st);
 // cluster: CTAs per thread-block cluster that share the slow-time operand by
-// multicast (1, 2, 4 or 8).
+// multicast (1, 2, 4 or 8).  mid: an event recorded between the operand builder and
+// the contraction kernel (profiling), or NULL.
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
                         int out_dtype, int grid, int cluster, bool use_partial, int num_sms,
-                        int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st);
+                        int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st,
+                        cudaEvent_t mid = nullptr);
 
 cudaError_t launch_range_doppler(const float2* const* cubes_dev, float2* tmp, float* power, int F,
                                  int V, int Ns, int L, int skip_static, double v_per_bin, float* v_est,

@@ -118,14 +118,12 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   FrameIO* table = (FrameIO*)(ws + off_table);
   int* counter = (int*)(ws + off_counter);
 
-  // the array keeps the previous call's contents: clear what must start at zero
-  e = cudaMemcpyAsync(table, &io, sizeof(FrameIO), cudaMemcpyHostToDevice, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(ws + off_meta, 0, 16, st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(counter, 0, 16, st);
-  if (e == cudaSuccess && !device_status) e = cudaMemsetAsync(status, 0, 4, st);
+  // the array keeps the previous call's contents: the first kernel stores the frame
+  // entry and clears the meta words and the unit counter; the status word is cleared here
+  if (!device_status) e = cudaMemsetAsync(status, 0, 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "static workspace set-up");
 
-  e = launch_prep(k, table, 1, P, pixels->dtype, false, status, st);
+  e = launch_prep(k, table, &io, 1, P, pixels->dtype, false, status, counter, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (tier == RSIM_TIER_FP32) {
     e = launch_direct(k, table, 1, splits, out_dtype, st);

@@ -50,6 +50,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_abi.rsim_pixels) == 16 + 6 * 8
     assert _abi.rsim_pixels.range.offset == 16
     assert ctypes.sizeof(_abi.rsim_plan) == 32
+    assert ctypes.sizeof(_abi.rsim_profile) == 8 + 4 * 8
     assert ctypes.sizeof(_abi.rsim_server_opts) == 16
     assert ctypes.sizeof(_abi.rsim_request) == 80 + 64 + 8 + 8
     assert ctypes.sizeof(_abi.rsim_server_stats) == 4 * 8 + 6 * 8 + 8 + 8
