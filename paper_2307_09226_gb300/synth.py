@@ -244,3 +244,107 @@ def point_scatterer(radar: Radar, R: float, sigma: complex, az: float, el: float
     """A single-pixel frame holding one point target."""
     a = lambda x: np.array([x], dtype=dtype)
     return Pixels(a(R), a(sigma.real), a(sigma.imag), a(az), a(el), a(vel))
+
+
+# ----------------------------------------------------------------------------------
+# Analytic scenes for the ray-caster (the rendering step of Section II).  A scene is a
+# list of primitive dicts: kind ("plane" | "capsule" | "ellipsoid"), vectors a, b, c,
+# d (metres), vel (m/s, of the pivot a), omega (rad/s, about a) and rho.  Radar at the
+# origin, x the array axis, y boresight, z up.
+# ----------------------------------------------------------------------------------
+
+PRIM_KINDS = ("plane", "capsule", "ellipsoid")
+CAMERA_FOV = ((np.deg2rad(-60.0), np.deg2rad(60.0)), (np.deg2rad(-30.0), np.deg2rad(30.0)))
+
+
+def _prim(kind, a, b=(0, 0, 0), c=(0, 0, 0), d=(0, 0, 0), vel=(0, 0, 0), omega=(0, 0, 0), rho=1.0):
+    f = lambda x: np.asarray(x, dtype=np.float64)
+    return {"kind": kind, "a": f(a), "b": f(b), "c": f(c), "d": f(d), "vel": f(vel), "omega": f(omega),
+            "rho": float(rho)}
+
+
+def _orthonormal(rng):
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    return q.T  # rows: three orthonormal vectors
+
+
+def random_scene(seed: int = 7, n_prims: int = 12):
+    """Random primitives in front of the radar: ellipsoids with random orientation and
+    semi-axes U(0.2, 0.8) m, capsules of radius U(0.05, 0.3) m and length U(0.3, 1.5) m,
+    and parallelograms with edges U(0.5, 3) m; centres at range U(1.5, 8) m within
+    +-50 deg azimuth and +-25 deg elevation; velocities U(-2, 2) m/s per axis, angular
+    velocities U(-3, 3) rad/s per axis, rho U(0.2, 1)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_prims):
+        kind = PRIM_KINDS[k % 3]
+        rr = rng.uniform(1.5, 8.0)
+        az = np.deg2rad(rng.uniform(-50, 50))
+        el = np.deg2rad(rng.uniform(-25, 25))
+        centre = rr * np.array([np.cos(el) * np.sin(az), np.cos(el) * np.cos(az), np.sin(el)])
+        vel = rng.uniform(-2, 2, 3)
+        om = rng.uniform(-3, 3, 3)
+        rho = rng.uniform(0.2, 1.0)
+        ax = _orthonormal(rng)
+        if kind == "ellipsoid":
+            s = rng.uniform(0.2, 0.8, 3)
+            out.append(_prim(kind, centre, ax[0] * s[0], ax[1] * s[1], ax[2] * s[2], vel, om, rho))
+        elif kind == "capsule":
+            half = 0.5 * rng.uniform(0.3, 1.5)
+            out.append(_prim(kind, centre - half * ax[0], centre + half * ax[0], (rng.uniform(0.05, 0.3), 0, 0),
+                             (0, 0, 0), vel, om, rho))
+        else:
+            e1, e2 = ax[0] * rng.uniform(0.5, 3.0), ax[1] * rng.uniform(0.5, 3.0)
+            out.append(_prim(kind, centre - 0.5 * (e1 + e2), e1, e2, (0, 0, 0), vel, om, rho))
+    return out
+
+
+def walking_scene(frame: int, n_frames: int = 100, fps: float = 24.0, radius: float = 3.0):
+    """A pedestrian walking a circle of `radius` m around a point 4 m in front of the
+    radar (one lap in n_frames frames at fps, the walking experiment of Section III),
+    in a room with a back wall at y = 8 m and a floor 1 m below the radar.
+
+    Body (capsules and one sphere, heights relative to the floor): torso from the hips
+    (0.95 m) to the neck (1.45 m), radius 0.16 m; head sphere of radius 0.11 m at
+    1.62 m; legs from the hips to the feet, arms from the shoulders (1.4 m) to the
+    hands, radius 0.06 m, swinging +-25 deg (legs) and +-20 deg (arms) at the step
+    rate of 2 steps per metre.  Returns (scene, ground truth) where ground truth holds
+    the torso position, its velocity vector and its closing speed towards the radar.
+    """
+    t = frame / fps
+    w = 2.0 * np.pi / (n_frames / fps)           # angular rate of the walk
+    speed = w * radius
+    cx, cy, floor = 0.0, 4.0, -1.0
+    ang = w * t
+    pos = np.array([cx + radius * np.cos(ang), cy + radius * np.sin(ang), floor])
+    fwd = np.array([-np.sin(ang), np.cos(ang), 0.0])
+    side = np.array([np.cos(ang), np.sin(ang), 0.0])
+    up = np.array([0.0, 0.0, 1.0])
+    v = speed * fwd
+    om_body = np.array([0.0, 0.0, w])            # the body turns with the path
+    step_w = 2.0 * np.pi * speed                 # one stride (two steps) per metre
+    scene = [
+        _prim("plane", (-6.0, 8.0, floor), (12.0, 0.0, 0.0), (0.0, 0.0, 3.0), rho=0.3),
+        _prim("plane", (-6.0, 0.5, floor), (12.0, 0.0, 0.0), (0.0, 7.5, 0.0), rho=0.2),
+    ]
+    hip = pos + 0.95 * up
+    neck = pos + 1.45 * up
+    scene.append(_prim("capsule", hip, neck, (0.16, 0, 0), vel=v, omega=om_body, rho=1.0))
+    head = pos + 1.62 * up
+    scene.append(_prim("ellipsoid", head, (0.11, 0, 0), (0, 0.11, 0), (0, 0, 0.11), vel=v, omega=om_body,
+                       rho=0.8))
+    for sgn, lim, amp, length, pivot_h, ph in ((1, "leg", 25.0, 0.9, 0.95, 0.0), (-1, "leg", 25.0, 0.9, 0.95, np.pi),
+                                               (1, "arm", 20.0, 0.6, 1.40, np.pi), (-1, "arm", 20.0, 0.6, 1.40, 0.0)):
+        pivot = pos + pivot_h * up + sgn * (0.1 if lim == "leg" else 0.22) * side
+        th = np.deg2rad(amp) * np.sin(step_w * t + ph)
+        thd = np.deg2rad(amp) * step_w * np.cos(step_w * t + ph)
+        end = pivot + length * (-np.cos(th) * up + np.sin(th) * fwd)
+        # the limb swings about the side axis on top of the body's turn; its pivot moves
+        # with the body: v_pivot = v + om_body x (pivot - pos)
+        v_piv = v + np.cross(om_body, pivot - pos)
+        om = om_body - thd * side
+        scene.append(_prim("capsule", pivot, end, (0.06, 0, 0), vel=v_piv, omega=om, rho=0.7))
+    centre = pos + 1.2 * up
+    los = centre / np.linalg.norm(centre)
+    truth = {"torso": centre, "vel_vec": v, "closing_speed": float(-(v @ los)), "speed": speed}
+    return scene, truth
