@@ -3,8 +3,8 @@ from .cube import (valid_mask, valid_indices, path_terms, phase_cycles, cube_lit
                    cube_separable, cube_entries, rel_l2)
 
 from .estimation import range_doppler_power, max_power_velocity, e_velo
-from .raycast import raycast, pixel_directions
+from . import raycast
 
 __all__ = ["valid_mask", "valid_indices", "path_terms", "phase_cycles", "cube_literal",
            "cube_separable", "cube_entries", "rel_l2", "range_doppler_power",
-           "max_power_velocity", "e_velo", "raycast", "pixel_directions"]
+           "max_power_velocity", "e_velo", "raycast"]
