@@ -222,6 +222,70 @@ rsim_status rsim_range_doppler(rsim_ctx* ctx, const rsim_radar_params* params, v
                                int32_t F, float* power, float* v_est, int32_t* peak, int32_t options,
                                rsim_stream stream);
 
+/* ---------------------------------------------------------------------------------
+ * Analytic-scene ray-caster: the rendering step that produces the per-pixel buffers
+ * the synthesis consumes (Section II: the light source sits at the Tx and the camera at
+ * the Rx, and every pixel of the N_az x N_el image gives a range, a strength, an angle
+ * of arrival and a velocity, the symbols after Eq. 2).
+ *
+ * Geometry: radar at the origin, x the horizontal array axis, y boresight, z up.  Pixel
+ * (i, j) of the cell-centred grid, p = j n_az + i, with
+ *   az_i = az_min + (i + 1/2) (az_max - az_min) / n_az,  el_j likewise,
+ * looks along d = (cos el sin az, cos el cos az, sin el), so d_x = cos(el) sin(az) is the
+ * direction cosine of the synthesis.  Per pixel:
+ *   range    = distance to the first surface with t > 0 along d, +inf when there is none;
+ *   sigma_re = rho |n . d| / range^2 (Lambert surface lit from the radar; without the
+ *              1/range^2 factor under RSIM_RC_NO_FALLOFF), sigma_im = 0; 0 for a miss;
+ *   az, el   = the pixel's angles;
+ *   vel      = -(vel + omega x (x - a)) . d, the closing speed of the surface point x the
+ *              ray meets (positive when it approaches the radar: the sign under which
+ *              Eq. 1's Doppler term f_D = 2 vel / lambda lowers the slow-time phase); 0
+ *              for a miss.
+ * A pixel whose distance ties between primitives takes the one listed first. */
+typedef enum { RSIM_PRIM_PLANE = 0, RSIM_PRIM_CAPSULE = 1, RSIM_PRIM_ELLIPSOID = 2 } rsim_prim_kind;
+
+typedef struct {
+  int32_t kind;       /* rsim_prim_kind */
+  int32_t reserved;
+  double a[3];        /* plane: corner; capsule: end A; ellipsoid: centre (the pivot of omega) */
+  double b[3];        /* plane: edge 1; capsule: end B; ellipsoid: semi-axis 1 */
+  double c[3];        /* plane: edge 2; capsule: c[0] = radius; ellipsoid: semi-axis 2 */
+  double d[3];        /* ellipsoid: semi-axis 3 (the three mutually orthogonal); else unused */
+  double vel[3];      /* linear velocity of the pivot a, m/s */
+  double omega[3];    /* angular velocity about a, rad/s */
+  double rho;         /* reflectivity (scale of the strength) */
+} rsim_primitive;     /* 160 bytes.  A plane is the two-sided parallelogram a + s b + t c,
+                         0 <= s, t <= 1; a capsule all points within c[0] of the segment
+                         a-b; an ellipsoid {a + sum_i s_i e_i : |s| <= 1}, e = (b, c, d) */
+
+typedef struct {
+  int32_t n_az, n_el;
+  double az_min, az_max;  /* rad */
+  double el_min, el_max;  /* rad */
+  int32_t flags;          /* RSIM_RC_NO_FALLOFF */
+  int32_t reserved;
+} rsim_camera;            /* 48 bytes */
+#define RSIM_RC_NO_FALLOFF 1
+
+/* Writable pixel buffers (same layout as rsim_pixels): P = n_az n_el elements each, of
+ * dtype RSIM_F32 (computed in FP32) or RSIM_F64 (computed in FP64).  DEVICE pointers. */
+typedef struct {
+  int64_t P;
+  int32_t dtype;
+  int32_t reserved;
+  void *range, *sigma_re, *sigma_im, *az, *el, *vel;
+} rsim_pixel_out;
+
+/* Render `n_prims` primitives (HOST array, read before the call returns; may be NULL
+ * when n_prims is 0) into `out`, whose arrays the caller owns.  INVALID_ARG for NULL
+ * pointers, n_az or n_el < 1, P != n_az n_el, an unknown kind or dtype, a non-finite
+ * number, a capsule radius <= 0 or coincident capsule ends, plane edges that are zero
+ * or (nearly) parallel (sine of their angle below 1e-6), or ellipsoid semi-axes that
+ * are zero or not mutually orthogonal (|e_i . e_j| > 1e-9 |e_i| |e_j|).
+ * Uses the context workspace.  Asynchronous on `stream`. */
+rsim_status rsim_raycast(rsim_ctx* ctx, const rsim_camera* cam, const rsim_primitive* prims,
+                         int32_t n_prims, const rsim_pixel_out* out, rsim_stream stream);
+
 /* Wait for `stream`, then return (and clear) the context's device-side status:
  * RSIM_OK, RSIM_ERR_NONFINITE or RSIM_ERR_TIMEOUT. */
 rsim_status rsim_sync_status(rsim_ctx* ctx, rsim_stream stream);

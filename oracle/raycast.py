@@ -119,8 +119,8 @@ def hit_capsule(d, prim):
     r = float(prim["c"][0])
     axis = b - a
     h2 = axis @ axis
-    # x(t) = t d; the part of x - a across the axis: (x - a) - ((x - a).axis / h2) axis
-    # |t d_perp - a_perp|^2 = r^2, with v_perp = v - (v.axis / h2) axis
+    # x(t) = t d; the part of x - a across the axis is t d_perp + ap with
+    # v_perp = v - (v . axis / h2) axis and ap = (0 - a)_perp: |t d_perp + ap|^2 = r^2
     dp = d - np.outer(d @ axis / h2, axis)
     ap = -a - (((-a) @ axis) / h2) * axis
     qa = (dp * dp).sum(axis=1)
@@ -166,7 +166,15 @@ def raycast(scene, n_az, n_el, az_range, el_range, falloff=True):
     """Render buffers of a scene: dict of P = n_az n_el arrays range, sigma_re,
     sigma_im, az, el, vel (FP64), with p = j n_az + i.  Ties between primitives at
     the same distance go to the one listed first."""
-    az, el, d = pixel_directions(n_az, n_el, az_range, el_range)
+    az, el, _ = pixel_directions(n_az, n_el, az_range, el_range)
+    return raycast_angles(scene, az, el, falloff)
+
+
+def raycast_angles(scene, az, el, falloff=True):
+    """The same for rays at arbitrary angles (arrays az, el)."""
+    az = np.asarray(az, float)
+    el = np.asarray(el, float)
+    d = np.stack([np.cos(el) * np.sin(az), np.cos(el) * np.cos(az), np.sin(el)], axis=1)
     P = d.shape[0]
     best = np.full(P, INF)
     which = np.full(P, -1)

@@ -45,6 +45,27 @@ class rsim_pixels(Structure):
                 ("az", c_void_p), ("el", c_void_p), ("vel", c_void_p)]
 
 
+class rsim_primitive(Structure):
+    _fields_ = [("kind", c_int32), ("reserved", c_int32), ("a", c_double * 3), ("b", c_double * 3),
+                ("c", c_double * 3), ("d", c_double * 3), ("vel", c_double * 3), ("omega", c_double * 3),
+                ("rho", c_double)]
+
+
+class rsim_camera(Structure):
+    _fields_ = [("n_az", c_int32), ("n_el", c_int32), ("az_min", c_double), ("az_max", c_double),
+                ("el_min", c_double), ("el_max", c_double), ("flags", c_int32), ("reserved", c_int32)]
+
+
+class rsim_pixel_out(Structure):
+    _fields_ = [("P", c_int64), ("dtype", c_int32), ("reserved", c_int32),
+                ("range", c_void_p), ("sigma_re", c_void_p), ("sigma_im", c_void_p),
+                ("az", c_void_p), ("el", c_void_p), ("vel", c_void_p)]
+
+
+PRIM_KINDS = {"plane": 0, "capsule": 1, "ellipsoid": 2}
+RC_NO_FALLOFF = 1
+
+
 class rsim_plan(Structure):
     _fields_ = [("splits", c_int32), ("chunk_px", c_int32), ("grid", c_int32),
                 ("variant", c_int32), ("tuned", c_int32), ("reserved", c_int32 * 3)]
@@ -94,6 +115,8 @@ SIGNATURES = {
     "rsim_sync_status": (c_int, [c_void_p, c_void_p]),
     "rsim_autotune": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
                               POINTER(rsim_plan), c_void_p]),
+    "rsim_raycast": (c_int, [c_void_p, POINTER(rsim_camera), POINTER(rsim_primitive), c_int32,
+                             POINTER(rsim_pixel_out), c_void_p]),
     "rsim_profile_enable": (c_int, [c_void_p, c_int32]),
     "rsim_profile_read": (c_int, [c_void_p, POINTER(rsim_profile)]),
     "rsim_set_plan": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
@@ -264,6 +287,32 @@ def rsim_autotune(ctx, radar, P: int, tier: int, stream=None) -> rsim_plan:
     check(load().rsim_autotune(ctx, ctypes.byref(radar_params(radar)), int(P), int(tier),
                                ctypes.byref(plan), _stream(stream)))
     return plan
+
+
+def primitives_struct(scene):
+    """A scene (list of primitive dicts with kind, a, b, c, d, vel, omega, rho) as an
+    array of rsim_primitive."""
+    arr = (rsim_primitive * max(len(scene), 1))()
+    for k, p in enumerate(scene):
+        q = arr[k]
+        q.kind = PRIM_KINDS[p["kind"]]
+        for f in ("a", "b", "c", "d", "vel", "omega"):
+            v = [float(x) for x in p[f]]
+            getattr(q, f)[:] = v
+        q.rho = float(p["rho"])
+    return arr
+
+
+def rsim_raycast(ctx, scene, n_az, n_el, fov, out, falloff=True, stream=None):
+    """Render `scene` into the six device tensors of `out` (dict, float32 or float64,
+    n_az * n_el elements each)."""
+    (az0, az1), (el0, el1) = fov
+    cam = rsim_camera(int(n_az), int(n_el), float(az0), float(az1), float(el0), float(el1),
+                      0 if falloff else RC_NO_FALLOFF, 0)
+    px = pixels_struct(out)
+    po = rsim_pixel_out(px.P, px.dtype, 0, px.range, px.sigma_re, px.sigma_im, px.az, px.el, px.vel)
+    prims = primitives_struct(scene)
+    check(load().rsim_raycast(ctx, ctypes.byref(cam), prims, len(scene), ctypes.byref(po), _stream(stream)))
 
 
 def rsim_profile_enable(ctx, on: bool):

@@ -61,6 +61,15 @@ class Context:
         _abi.rsim_synth_batch(self.h, radar, frames, t, cubes, stream)
         return cubes
 
+    def raycast(self, scene, n_az, n_el, fov, dtype=torch.float32, falloff=True, out=None, stream=None):
+        """Render an analytic scene into per-pixel buffers (dict of six device tensors,
+        the input of synth)."""
+        P = int(n_az) * int(n_el)
+        if out is None:
+            out = {k: torch.empty(P, dtype=dtype, device="cuda") for k in FIELDS}
+        _abi.rsim_raycast(self.h, scene, n_az, n_el, fov, out, falloff, stream)
+        return out
+
     def valid_indices(self, pixels, stream=None):
         P = int(pixels["range"].numel())
         idx = torch.full((max(P, 1),), -1, dtype=torch.int32, device="cuda")

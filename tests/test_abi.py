@@ -51,6 +51,9 @@ def test_struct_layouts_match_header():
     assert _abi.rsim_pixels.range.offset == 16
     assert ctypes.sizeof(_abi.rsim_plan) == 32
     assert ctypes.sizeof(_abi.rsim_profile) == 8 + 4 * 8
+    assert ctypes.sizeof(_abi.rsim_primitive) == 8 + 6 * 24 + 8
+    assert ctypes.sizeof(_abi.rsim_camera) == 8 + 4 * 8 + 8
+    assert ctypes.sizeof(_abi.rsim_pixel_out) == ctypes.sizeof(_abi.rsim_pixels)
     assert ctypes.sizeof(_abi.rsim_server_opts) == 16
     assert ctypes.sizeof(_abi.rsim_request) == 80 + 64 + 8 + 8
     assert ctypes.sizeof(_abi.rsim_server_stats) == 4 * 8 + 6 * 8 + 8 + 8
