@@ -63,6 +63,16 @@ class rsim_pixel_out(Structure):
 
 
 PRIM_KINDS = {"plane": 0, "capsule": 1, "ellipsoid": 2}
+
+
+def _prim_dtype():
+    import numpy as np
+    return np.dtype([("kind", "<i4"), ("reserved", "<i4"), ("a", "<f8", (3,)), ("b", "<f8", (3,)),
+                     ("c", "<f8", (3,)), ("d", "<f8", (3,)), ("vel", "<f8", (3,)), ("omega", "<f8", (3,)),
+                     ("rho", "<f8")])
+
+
+PRIM_DTYPE = _prim_dtype()
 RC_NO_FALLOFF = 1
 
 
@@ -289,17 +299,18 @@ def rsim_autotune(ctx, radar, P: int, tier: int, stream=None) -> rsim_plan:
     return plan
 
 
-def primitives_struct(scene):
-    """A scene (list of primitive dicts with kind, a, b, c, d, vel, omega, rho) as an
-    array of rsim_primitive."""
-    arr = (rsim_primitive * max(len(scene), 1))()
-    for k, p in enumerate(scene):
-        q = arr[k]
-        q.kind = PRIM_KINDS[p["kind"]]
+def primitives_array(scene):
+    """A scene (list of primitive dicts with kind, a, b, c, d, vel, omega, rho) as a numpy
+    structured array laid out like rsim_primitive (an array passes through unchanged)."""
+    import numpy as np
+    if isinstance(scene, np.ndarray) and scene.dtype == PRIM_DTYPE:
+        return np.ascontiguousarray(scene)
+    arr = np.zeros(len(scene), dtype=PRIM_DTYPE)
+    if len(scene):
+        arr["kind"] = [PRIM_KINDS[p["kind"]] for p in scene]
         for f in ("a", "b", "c", "d", "vel", "omega"):
-            v = [float(x) for x in p[f]]
-            getattr(q, f)[:] = v
-        q.rho = float(p["rho"])
+            arr[f] = [p[f] for p in scene]
+        arr["rho"] = [p["rho"] for p in scene]
     return arr
 
 
@@ -311,8 +322,9 @@ def rsim_raycast(ctx, scene, n_az, n_el, fov, out, falloff=True, stream=None):
                       0 if falloff else RC_NO_FALLOFF, 0)
     px = pixels_struct(out)
     po = rsim_pixel_out(px.P, px.dtype, 0, px.range, px.sigma_re, px.sigma_im, px.az, px.el, px.vel)
-    prims = primitives_struct(scene)
-    check(load().rsim_raycast(ctx, ctypes.byref(cam), prims, len(scene), ctypes.byref(po), _stream(stream)))
+    arr = primitives_array(scene)
+    ptr = arr.ctypes.data_as(POINTER(rsim_primitive)) if arr.size else None
+    check(load().rsim_raycast(ctx, ctypes.byref(cam), ptr, int(arr.size), ctypes.byref(po), _stream(stream)))
 
 
 def rsim_profile_enable(ctx, on: bool):

@@ -3,15 +3,14 @@
 // the Tx and the camera at the Rx).  See include/rsim.h for the geometry and the
 // definition of each output.
 //
-// Two kernels:
-//   rc_setup  - one thread per primitive derives the per-primitive constants of its
-//               intersection test in FP64 (unit normals, the dual basis of a plane, the
-//               unit-sphere frame of an ellipsoid, the constant terms of the quadratics)
-//               and stores them in the compute precision T;
-//   rc_render - one thread per pixel: the ray direction from the pixel's angles, the
-//               first positive hit over all primitives (tiles of primitives staged in
-//               shared memory), then normal, Lambert strength and closing speed at the
-//               hit point.  T = float for FP32 buffers, double for FP64 buffers.
+// One kernel, rc_render, one thread per pixel: the ray direction from the pixel's
+// angles, the first positive hit over all primitives, then normal, Lambert strength
+// and closing speed at the hit point.  The primitives are staged in shared memory in
+// tiles of 64, each thread of a block deriving one primitive's constants (unit normal,
+// the dual basis of a plane, the unit-sphere frame of an ellipsoid, the constant terms
+// of the quadratics) in the compute precision T = float for FP32 buffers, double for
+// FP64 buffers.  A plane's in-plane coordinates use the dual basis b* = (c x n) / |n|^2,
+// c* = (n x b) / |n|^2 (n = b x c), which needs no Gram determinant.
 // Every curved surface is met as a sphere in some frame (the end caps as they are, the
 // cylinder in the plane across its axis, the ellipsoid in its unit-sphere frame).  The
 // roots of |f + t u|^2 = rr (u a unit vector) take the discriminant from the distance
@@ -37,7 +36,8 @@ template <typename T>
 struct RcPrim {
   int kind;
   T a[3], v[3], om[3], rho;
-  // plane:     e0 = b, e1 = c, e2 = unit normal; k0 = a . n, (k1, k2, k3) = (c.c, b.b, b.c) / det
+  // plane:     e0 = b*, e1 = c* (dual basis: (x - a) = s b + u c gives s = (x - a) . b*,
+  //            u = (x - a) . c*), e2 = unit normal; k0 = a . e2
   // capsule:   e0 = b - a (axis), e1 = ap (the origin's offset from the axis line, across
   //            it), e2 = b; k0 = |ap|^2 - r^2, k1 = |a|^2 - r^2, k2 = |b|^2 - r^2, k3 = 1 / |axis|^2
   // ellipsoid: e0, e1, e2 = e_i / |e_i|^2 (the unit-sphere frame); (k0, k1, k2) = s0 = -a . w_i,
@@ -47,85 +47,76 @@ struct RcPrim {
   T rr;  // capsule: r^2
 };
 
-__device__ __forceinline__ double dot3(const double* x, const double* y) {
-  return x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
-}
-
 template <typename T>
 __device__ __forceinline__ T dot3t(const T* x, const T* y) {
   return x[0] * y[0] + x[1] * y[1] + x[2] * y[2];
 }
 
 template <typename T>
-__global__ void rc_setup(const rsim_primitive* __restrict__ raw, int n, RcPrim<T>* __restrict__ out) {
-  wait_prior_grid();
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const rsim_primitive& p = raw[k];
-  RcPrim<T> q;
-  q.kind = p.kind;
+__device__ __forceinline__ void cross3(const T* x, const T* y, T* z) {
+  z[0] = x[1] * y[2] - x[2] * y[1];
+  z[1] = x[2] * y[0] - x[0] * y[2];
+  z[2] = x[0] * y[1] - x[1] * y[0];
+}
+
+// The per-primitive constants of the intersection test, in T.
+template <typename T>
+__device__ void derive(const rsim_primitive& p, RcPrim<T>& q) {
+  T a[3], b[3], c[3], d[3];
   for (int i = 0; i < 3; ++i) {
-    q.a[i] = (T)p.a[i];
+    a[i] = (T)p.a[i];
+    b[i] = (T)p.b[i];
+    c[i] = (T)p.c[i];
+    d[i] = (T)p.d[i];
+    q.a[i] = a[i];
     q.v[i] = (T)p.vel[i];
     q.om[i] = (T)p.omega[i];
   }
+  q.kind = p.kind;
   q.rho = (T)p.rho;
-  double e0[3] = {0, 0, 0}, e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
-  double k0 = 0, k1 = 0, k2 = 0, k3 = 0;
+  q.k0 = q.k1 = q.k2 = q.k3 = (T)0;
+  q.rr = (T)1;
   if (p.kind == RSIM_PRIM_PLANE) {
-    double n[3] = {p.b[1] * p.c[2] - p.b[2] * p.c[1], p.b[2] * p.c[0] - p.b[0] * p.c[2],
-                   p.b[0] * p.c[1] - p.b[1] * p.c[0]};
-    const double nn = sqrt(dot3(n, n));
+    T n[3], cn[3], nb[3];
+    cross3(b, c, n);
+    const T nn = dot3t(n, n), ln = sqrt(nn);
+    cross3(c, n, cn);
+    cross3(n, b, nb);
     for (int i = 0; i < 3; ++i) {
-      e0[i] = p.b[i];
-      e1[i] = p.c[i];
-      e2[i] = n[i] / nn;
+      q.e0[i] = cn[i] / nn;
+      q.e1[i] = nb[i] / nn;
+      q.e2[i] = n[i] / ln;
     }
-    const double bb = dot3(p.b, p.b), cc = dot3(p.c, p.c), bc = dot3(p.b, p.c);
-    const double det = bb * cc - bc * bc;
-    k0 = dot3(p.a, e2);
-    k1 = cc / det;
-    k2 = bb / det;
-    k3 = bc / det;
+    q.k0 = dot3t(a, q.e2);
   } else if (p.kind == RSIM_PRIM_CAPSULE) {
-    const double r = p.c[0];
-    double ax[3] = {p.b[0] - p.a[0], p.b[1] - p.a[1], p.b[2] - p.a[2]};
-    const double h2 = dot3(ax, ax);
-    const double f = -dot3(p.a, ax) / h2;  // (origin - a) . axis / h2
+    const T r = c[0];
+    T ax[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    const T h2 = dot3t(ax, ax);
+    const T f = -dot3t(a, ax) / h2;  // (origin - a) . axis / h2
     for (int i = 0; i < 3; ++i) {
-      e0[i] = ax[i];
-      e1[i] = -p.a[i] - f * ax[i];
-      e2[i] = p.b[i];
+      q.e0[i] = ax[i];
+      q.e1[i] = -a[i] - f * ax[i];
+      q.e2[i] = b[i];
     }
-    k0 = dot3(e1, e1) - r * r;
-    k1 = dot3(p.a, p.a) - r * r;
-    k2 = dot3(p.b, p.b) - r * r;
-    k3 = 1.0 / h2;
+    q.rr = r * r;
+    q.k0 = dot3t(q.e1, q.e1) - q.rr;
+    q.k1 = dot3t(a, a) - q.rr;
+    q.k2 = dot3t(b, b) - q.rr;
+    q.k3 = (T)1 / h2;
   } else {  // ellipsoid
-    const double* E[3] = {p.b, p.c, p.d};
-    double* W[3] = {e0, e1, e2};
-    double s0[3];
+    const T* E[3] = {b, c, d};
+    T* W[3] = {q.e0, q.e1, q.e2};
+    T s0[3];
     for (int i = 0; i < 3; ++i) {
-      const double ee = dot3(E[i], E[i]);
+      const T ee = dot3t(E[i], E[i]);
       for (int j = 0; j < 3; ++j) W[i][j] = E[i][j] / ee;
-      s0[i] = -dot3(p.a, W[i]);
+      s0[i] = -dot3t(a, W[i]);
     }
-    k0 = s0[0];
-    k1 = s0[1];
-    k2 = s0[2];
-    k3 = dot3(s0, s0) - 1.0;
+    q.k0 = s0[0];
+    q.k1 = s0[1];
+    q.k2 = s0[2];
+    q.k3 = dot3t(s0, s0) - (T)1;
   }
-  for (int i = 0; i < 3; ++i) {
-    q.e0[i] = (T)e0[i];
-    q.e1[i] = (T)e1[i];
-    q.e2[i] = (T)e2[i];
-  }
-  q.k0 = (T)k0;
-  q.k1 = (T)k1;
-  q.k2 = (T)k2;
-  q.k3 = (T)k3;
-  q.rr = (T)(p.kind == RSIM_PRIM_CAPSULE ? p.c[0] * p.c[0] : 1.0);
-  out[k] = q;
 }
 
 template <typename T>
@@ -169,8 +160,7 @@ __device__ T hit(const RcPrim<T>& p, const T* d) {
     const T t = p.k0 / dn;
     if (!(t > (T)0)) return t_inf<T>();
     T x[3] = {t * d[0] - p.a[0], t * d[1] - p.a[1], t * d[2] - p.a[2]};
-    const T xb = dot3t(x, p.e0), xc = dot3t(x, p.e1);
-    const T s = p.k1 * xb - p.k3 * xc, u = p.k2 * xc - p.k3 * xb;
+    const T s = dot3t(x, p.e0), u = dot3t(x, p.e1);
     return (s >= (T)0 && s <= (T)1 && u >= (T)0 && u <= (T)1) ? t : t_inf<T>();
   }
   if (p.kind == RSIM_PRIM_CAPSULE) {
@@ -230,7 +220,7 @@ __device__ void normal_at(const RcPrim<T>& p, const T* x, T* n) {
 
 template <typename T>
 __global__ void __launch_bounds__(kRcThreads)
-rc_render(const RcPrim<T>* __restrict__ prims, int n_prims, int n_az, int n_el, double az0, double az1,
+rc_render(const rsim_primitive* __restrict__ prims, int n_prims, int n_az, int n_el, double az0, double az1,
           double el0, double el1, int falloff, T* __restrict__ R, T* __restrict__ sre, T* __restrict__ sim,
           T* __restrict__ az_out, T* __restrict__ el_out, T* __restrict__ vel) {
   wait_prior_grid();
@@ -261,7 +251,7 @@ rc_render(const RcPrim<T>* __restrict__ prims, int n_prims, int n_az, int n_el, 
   for (int k0 = 0; k0 < n_prims; k0 += kRcTile) {
     const int nt = min(kRcTile, n_prims - k0);
     __syncthreads();
-    for (int k = threadIdx.x; k < nt; k += blockDim.x) tile[k] = prims[k0 + k];
+    for (int k = threadIdx.x; k < nt; k += blockDim.x) derive(prims[k0 + k], tile[k]);
     __syncthreads();
     if (live) {
       for (int k = 0; k < nt; ++k) {
@@ -276,7 +266,11 @@ rc_render(const RcPrim<T>* __restrict__ prims, int n_prims, int n_az, int n_el, 
   if (!live) return;
   T r = t_inf<T>(), s = (T)0, w = (T)0;
   if (which >= 0) {
-    const RcPrim<T> q = prims[which];
+    RcPrim<T> q;
+    if (n_prims <= kRcTile)
+      q = tile[which];  // the only tile is still staged
+    else
+      derive(prims[which], q);
     r = best;
     const T x[3] = {r * d[0], r * d[1], r * d[2]};
     T n[3];
@@ -327,18 +321,12 @@ std::string check_prim(const rsim_primitive& p) {
 }
 
 template <typename T>
-cudaError_t launch_raycast(const rsim_primitive* raw, int n, RcPrim<T>* derived, const rsim_camera& cam,
-                           const rsim_pixel_out& out, cudaStream_t st) {
-  const int64_t P = out.P;
-  if (n > 0) {
-    rc_setup<T><<<(n + 127) / 128, 128, 0, st>>>(raw, n, derived);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  const int64_t blocks = (P + kRcThreads - 1) / kRcThreads;
-  return launch_dependent(rc_render<T>, dim3((unsigned)blocks), dim3(kRcThreads), 0, st,
-                          (const RcPrim<T>*)derived, n, cam.n_az, cam.n_el, cam.az_min, cam.az_max, cam.el_min,
-                          cam.el_max, (cam.flags & RSIM_RC_NO_FALLOFF) ? 0 : 1, (T*)out.range, (T*)out.sigma_re,
+cudaError_t launch_raycast(const rsim_primitive* raw, int n, const rsim_camera& cam, const rsim_pixel_out& out,
+                           cudaStream_t st) {
+  const int64_t blocks = (out.P + kRcThreads - 1) / kRcThreads;
+  return launch_dependent(rc_render<T>, dim3((unsigned)blocks), dim3(kRcThreads), 0, st, raw, n, cam.n_az,
+                          cam.n_el, cam.az_min, cam.az_max, cam.el_min, cam.el_max,
+                          (cam.flags & RSIM_RC_NO_FALLOFF) ? 0 : 1, (T*)out.range, (T*)out.sigma_re,
                           (T*)out.sigma_im, (T*)out.az, (T*)out.el, (T*)out.vel);
 }
 
@@ -368,8 +356,7 @@ extern "C" rsim_status rsim_raycast(rsim_ctx* ctx, const rsim_camera* cam, const
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
   const size_t raw_bytes = ((sizeof(rsim_primitive) * (size_t)n_prims + 255) / 256) * 256;
-  const size_t der_bytes = sizeof(RcPrim<double>) * (size_t)n_prims;
-  rsim_status s = ensure_workspace(ctx, raw_bytes + der_bytes + 256, st);
+  rsim_status s = ensure_workspace(ctx, raw_bytes + 256, st);
   if (s != RSIM_OK) return s;
   char* ws = (char*)ctx->ws;
   cudaError_t e = cudaSuccess;
@@ -379,9 +366,9 @@ extern "C" rsim_status rsim_raycast(rsim_ctx* ctx, const rsim_camera* cam, const
   }
   const rsim_primitive* raw = (const rsim_primitive*)ws;
   if (out->dtype == RSIM_F32)
-    e = launch_raycast<float>(raw, n_prims, (RcPrim<float>*)(ws + raw_bytes), *cam, *out, st);
+    e = launch_raycast<float>(raw, n_prims, *cam, *out, st);
   else
-    e = launch_raycast<double>(raw, n_prims, (RcPrim<double>*)(ws + raw_bytes), *cam, *out, st);
+    e = launch_raycast<double>(raw, n_prims, *cam, *out, st);
   if (e != cudaSuccess) return cuda_fail(e, "ray-caster kernels");
   return RSIM_OK;
 }

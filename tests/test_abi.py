@@ -52,6 +52,9 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_abi.rsim_plan) == 32
     assert ctypes.sizeof(_abi.rsim_profile) == 8 + 4 * 8
     assert ctypes.sizeof(_abi.rsim_primitive) == 8 + 6 * 24 + 8
+    assert _abi.PRIM_DTYPE.itemsize == ctypes.sizeof(_abi.rsim_primitive)
+    for name, _ in _abi.rsim_primitive._fields_:
+        assert _abi.PRIM_DTYPE.fields[name][1] == getattr(_abi.rsim_primitive, name).offset
     assert ctypes.sizeof(_abi.rsim_camera) == 8 + 4 * 8 + 8
     assert ctypes.sizeof(_abi.rsim_pixel_out) == ctypes.sizeof(_abi.rsim_pixels)
     assert ctypes.sizeof(_abi.rsim_server_opts) == 16
