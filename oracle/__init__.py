@@ -4,7 +4,8 @@ from .cube import (valid_mask, valid_indices, path_terms, phase_cycles, cube_lit
 
 from .estimation import range_doppler_power, max_power_velocity, e_velo
 from . import raycast
+from . import nufft
 
 __all__ = ["valid_mask", "valid_indices", "path_terms", "phase_cycles", "cube_literal",
            "cube_separable", "cube_entries", "rel_l2", "range_doppler_power",
-           "max_power_velocity", "e_velo", "raycast"]
+           "max_power_velocity", "e_velo", "raycast", "nufft"]
