@@ -70,7 +70,11 @@ typedef enum {
   RSIM_TIER_BF16 = 1,       /* tcgen05 tensor cores, BF16 operands, FP32 accumulate */
   RSIM_TIER_SPLIT_BF16 = 2, /* tcgen05, BF16 hi+lo operands (3 products), FP32 accumulate */
   RSIM_TIER_SPLIT_FP16 = 3, /* tcgen05, FP16 hi+lo operands (3 products), FP32 accumulate */
-  RSIM_TIER_FP16 = 4        /* tcgen05, FP16 operands, FP32 accumulate */
+  RSIM_TIER_FP16 = 4,       /* tcgen05, FP16 operands, FP32 accumulate */
+  RSIM_TIER_NUFFT = 5       /* type-1 non-uniform FFT per channel on CUDA cores: ES-kernel
+                               gridding (width 7, oversampling >= 2) with exact fixed-point
+                               sums, FP32 FFTs; relative error ~1e-6.  N_s and L in 4..2048
+                               (else UNSUPPORTED) */
 } rsim_tier;
 
 /* Element type of the pixel arrays (all six share it). */

@@ -18,9 +18,9 @@ OK, ERR_INVALID_ARG, ERR_NONFINITE, ERR_OVERFLOW, ERR_OOM, ERR_BUDGET, ERR_TIMEO
     ERR_CANCELLED, ERR_CUDA, ERR_UNSUPPORTED, ERR_NOT_FOUND = range(11)
 STATUS_NAMES = ["OK", "INVALID_ARG", "NONFINITE", "OVERFLOW", "OOM", "BUDGET", "TIMEOUT",
                 "CANCELLED", "CUDA", "UNSUPPORTED", "NOT_FOUND"]
-TIER_FP32, TIER_BF16, TIER_SPLIT_BF16, TIER_SPLIT_FP16, TIER_FP16 = range(5)
+TIER_FP32, TIER_BF16, TIER_SPLIT_BF16, TIER_SPLIT_FP16, TIER_FP16, TIER_NUFFT = range(6)
 TIERS = {"fp32": TIER_FP32, "bf16": TIER_BF16, "split_bf16": TIER_SPLIT_BF16,
-         "split_fp16": TIER_SPLIT_FP16, "fp16": TIER_FP16}
+         "split_fp16": TIER_SPLIT_FP16, "fp16": TIER_FP16, "nufft": TIER_NUFFT}
 F32, F64 = 0, 1
 FLAG_TDM_MOTION = 1
 C64, C128 = 0, 1

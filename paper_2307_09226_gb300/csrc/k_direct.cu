@@ -225,6 +225,7 @@ cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int spl
 }
 
 bool uses_partial(int tier, int64_t P, int splits) {
+  if (tier == RSIM_TIER_NUFFT) return false;
   if (splits > 1) return true;
   if (tier == RSIM_TIER_FP32) return false;
   const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
@@ -243,6 +244,7 @@ int units_per_split(int tier, int V, int Ns, int L) {
 }
 
 int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms) {
+  if (tier == RSIM_TIER_NUFFT) return 1;
   const int tiles = units_per_split(tier, V, Ns, L);
   const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
   // keep at least 8 chunks (256 pixels) per split

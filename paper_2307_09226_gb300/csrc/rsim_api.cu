@@ -111,7 +111,7 @@ rsim_status check_pixels(const rsim_pixels* px) {
   return RSIM_OK;
 }
 
-bool tier_ok(int tier) { return tier >= RSIM_TIER_FP32 && tier <= RSIM_TIER_FP16; }
+bool tier_ok(int tier) { return tier >= RSIM_TIER_FP32 && tier <= RSIM_TIER_NUFFT; }
 
 std::string plan_key(int tier, const Consts& k, int64_t P) {
   char b[160];
@@ -137,8 +137,8 @@ rsim_plan choose_plan(rsim_ctx* ctx, int tier, const Consts& k, int64_t P) {
   return p;
 }
 
-// Workspace bytes for F frames of P_f pixels with the given splits.
-size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits, int tier) {
+// Workspace bytes of the per-frame regions of F frames of P_f pixels.
+size_t frames_bytes(const Consts& k, const int64_t* P, int F, int splits, int tier) {
   int64_t mp = 0;
   for (int f = 0; f < F; ++f) mp = std::max(mp, P[f]);
   const bool up = uses_partial(tier, mp, splits);
@@ -146,8 +146,20 @@ size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits, int tie
   o = align_up(o + 16 * (size_t)F, 256);                  // meta
   o = align_up(o + 16 + 4 * (size_t)F, 256);              // unit counter + frame order
   for (int f = 0; f < F; ++f) {
-    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], splits, up, tier != RSIM_TIER_FP32, o);
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], splits, up, tensor_tier(tier), o);
     o = fl.total;
+  }
+  return o;
+}
+
+// Workspace bytes for F frames: the per-frame regions, then (NUFFT tier) one grid
+// scratch that the frames use in turn.
+size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits, int tier) {
+  size_t o = frames_bytes(k, P, F, splits, tier);
+  if (tier == RSIM_TIER_NUFFT) {
+    int64_t mp = 0;
+    for (int f = 0; f < F; ++f) mp = std::max(mp, P[f]);
+    o = align_up(o, 256) + nufft_scratch_bytes(k, mp);
   }
   return o;
 }
@@ -243,7 +255,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   FrameIO* table = nullptr;
   int* counter = nullptr;
   rsim_status s = stage_frames(ctx, ws, k, frames, F, cubes, splits, use_partial,
-                               tier != RSIM_TIER_FP32, st, host, &table, &counter);
+                               tensor_tier(tier), st, host, &table, &counter);
   if (s != RSIM_OK) return s;
   // stage events when profiling this context's own calls
   // ev: start, after compaction + phases, after the contraction, after the reduction,
@@ -262,15 +274,25 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     // compaction + phases (2); FP32: direct sum (1); tensor tiers: operand builder (1 when
     // a frame has valid pixels), frame order (1 for a batch), contraction (1); the split
     // reduction (1 when the partial buffer is used)
-    const bool tensor = tier != RSIM_TIER_FP32;
-    ctx->prof_kernels += 2 + (tensor ? 1 + (mp > 0 ? 1 : 0) + (F > 1 ? 1 : 0) : 1) + (use_partial ? 1 : 0);
+    const bool tensor = tensor_tier(tier);
+    ctx->prof_kernels += 2 + (tier == RSIM_TIER_NUFFT ? 7 * F
+                              : tensor ? 1 + (mp > 0 ? 1 : 0) + (F > 1 ? 1 : 0) : 1) + (use_partial ? 1 : 0);
     cudaEventRecord(ev[0], st);
   }
   cudaError_t e = launch_prep(k, table, F == 1 ? host.data() : nullptr, F, mp, frames[0].dtype, false, status,
                               counter, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (prof) cudaEventRecord(ev[1], st);
-  if (tier == RSIM_TIER_FP32) {
+  if (tier == RSIM_TIER_NUFFT) {
+    if (prof) cudaEventRecord(ev[4], st);
+    if (!nufft_supported(k)) return fail(RSIM_ERR_UNSUPPORTED, "the NUFFT tier needs N_s and L in 4..2048");
+    char* scratch = ws + align_up(frames_bytes(k, Ps.data(), F, splits, tier), 256);
+    for (int f = 0; f < F; ++f) {
+      e = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch, st);
+      if (e != cudaSuccess) return cuda_fail(e, "NUFFT kernels");
+    }
+    if (prof) cudaEventRecord(ev[2], st);
+  } else if (tier == RSIM_TIER_FP32) {
     if (prof) cudaEventRecord(ev[4], st);
     e = launch_direct(k, table, F, splits, out_dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
@@ -385,7 +407,7 @@ rsim_status rsim_synth_batch(rsim_ctx* ctx, const rsim_radar_params* params,
       return fail(RSIM_ERR_INVALID_ARG, "all frames of a batch must share the pixel dtype");
     maxp = std::max(maxp, frames[f].P);
   }
-  if (tier != RSIM_TIER_FP32 && !(ctx->cc_major == 10 && ctx->cc_minor == 3))
+  if (tensor_tier(tier) && !(ctx->cc_major == 10 && ctx->cc_minor == 3))
     return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tiers need an sm_103 device");
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");

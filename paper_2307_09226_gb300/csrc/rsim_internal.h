@@ -71,6 +71,29 @@ int tile_nt(int L);
 // that a warp's 32 accumulator rows drain into 512 contiguous bytes.
 int64_t tensor_split_stride(int V, int Ns, int L);
 
+// Tensor-core tiers (the tcgen05 contraction and its operand images).
+inline bool tensor_tier(int tier) {
+  return tier == RSIM_TIER_BF16 || tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16 ||
+         tier == RSIM_TIER_FP16;
+}
+
+// NUFFT tier: grid and tile geometry of one frame shape.
+struct NuGeo {
+  int V, Ns, L;   // channels and output modes
+  int Gx, Gy;     // oversampled grid (powers of two >= 2 Ns, 2 L)
+  int Tx, Ty;     // tile sides (cells)
+  int ntx, nty;   // tiles per axis
+  int sx, sy;     // centring shifts Ns / 2, L / 2
+  int64_t P;      // pixel bound (items per channel)
+};
+NuGeo nufft_geometry(const Consts& k, int64_t P);
+bool nufft_supported(const Consts& k);
+size_t nufft_scratch_bytes(const Consts& k, int64_t P);
+// One frame (`frame`: device pointer to its table entry, P: its pixel count), using
+// nufft_scratch_bytes(k, P) bytes of scratch.
+cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int out_dtype, char* scratch,
+                         cudaStream_t st);
+
 // Programmatic dependent launch: a kernel launched with launch_dependent may be
 // scheduled while the previous kernel in the stream drains its last blocks, hiding the
 // launch latency between the stages of one call.  Such a kernel executes

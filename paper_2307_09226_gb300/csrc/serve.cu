@@ -256,7 +256,7 @@ rsim_status rsim_server_submit(rsim_server* s, const rsim_request* req, uint64_t
   if (req->out_dtype != RSIM_C64 && req->out_dtype != RSIM_C128)
     return fail(RSIM_ERR_INVALID_ARG, "out_dtype must be RSIM_C64 or RSIM_C128");
   if (!req->cube) return fail(RSIM_ERR_INVALID_ARG, "cube is NULL");
-  if (req->tier != RSIM_TIER_FP32 && !(s->ctx->cc_major == 10 && s->ctx->cc_minor == 3))
+  if (tensor_tier(req->tier) && !(s->ctx->cc_major == 10 && s->ctx->cc_minor == 3))
     return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tiers need an sm_103 device");
   r.plan = choose_plan(s->ctx, req->tier, r.k, req->pixels.P);
   int64_t P = req->pixels.P;

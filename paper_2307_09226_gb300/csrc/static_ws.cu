@@ -68,7 +68,8 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (e != cudaSuccess) return cuda_fail(e, "device query");
-  if (tier != RSIM_TIER_FP32 && !(major == 10 && minor == 3))
+  if (tier == RSIM_TIER_NUFFT) return fail(RSIM_ERR_UNSUPPORTED, "the static workspace serves the direct and tensor-core tiers");
+  if (tensor_tier(tier) && !(major == 10 && minor == 3))
     return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tiers need an sm_103 device");
 
   // the plan is the library's default rule for this shape (what rsim_synth uses
@@ -80,7 +81,7 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   const size_t off_table = o;   o = up256(o + sizeof(FrameIO));
   const size_t off_meta = o;    o = up256(o + 16);
   const size_t off_counter = o; o = up256(o + 16 + 4);
-  FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P, splits, use_partial, tier != RSIM_TIER_FP32, o);
+  FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P, splits, use_partial, tensor_tier(tier), o);
   o = fl.total;
   const size_t off_status = o;  o = up256(o + 4);
   if (o > kStaticWsBytes)
@@ -112,7 +113,7 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   io.blk_count = (int32_t*)(ws + fl.blk);
   io.meta = (unsigned long long*)(ws + off_meta);
   io.partial = use_partial ? (float2*)(ws + fl.partial) : nullptr;
-  io.bimg = tier != RSIM_TIER_FP32 ? (unsigned char*)(ws + fl.bimg) : nullptr;
+  io.bimg = tensor_tier(tier) ? (unsigned char*)(ws + fl.bimg) : nullptr;
   io.bimg_nch = fl.bimg_nch;
   io.splits = splits;
   FrameIO* table = (FrameIO*)(ws + off_table);

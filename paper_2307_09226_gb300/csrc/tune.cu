@@ -141,7 +141,7 @@ extern "C" rsim_status rsim_autotune(rsim_ctx* ctx, const rsim_radar_params* par
     if (std::find(cand_s.begin(), cand_s.end(), a) == cand_s.end()) cand_s.push_back(a);
   }
   std::vector<int> cand_g = {0};
-  if (tier != RSIM_TIER_FP32) cand_g = {ctx->num_sms, ctx->num_sms / 2};
+  if (tensor_tier(tier)) cand_g = {ctx->num_sms, ctx->num_sms / 2};
 
   // synthetic pixels and an output buffer
   float* px = nullptr;

@@ -1,0 +1,70 @@
+"""GPU NUFFT tier: agreement with the CPU NUFFT reference at the same kernel width
+(implementation error only), repeat runs and batches bit-identical to single frames,
+empty frames, crowded grids, and the size limits."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import oracle.nufft as nu
+from paper_2307_09226_gb300 import _abi, device, synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = device.Context(0)
+    yield c
+    c.close()
+
+
+def test_gpu_matches_cpu_nufft_at_width_7(ctx):
+    # both compute the same gridding approximation; the GPU adds FP32 rounding only
+    f = synth.parity_frame(seed=41, M=2, N=2, Ns=128, L=64, n_az=90, n_el=60)
+    got = ctx.synth(f.radar, device.upload(f), "nufft").cpu().numpy()
+    cpu = nu.cube_nufft(f.radar, f.pixels, w=7)
+    ref = oracle.cube_separable(f.radar, f.pixels)
+    e_impl, e_cpu, e_gpu = oracle.rel_l2(got, cpu), oracle.rel_l2(cpu, ref), oracle.rel_l2(got, ref)
+    print(f"gpu vs cpu nufft {e_impl:.2e}, cpu nufft vs exact {e_cpu:.2e}, gpu vs exact {e_gpu:.2e}")
+    assert e_impl <= 5e-6
+    assert e_gpu <= 2e-5
+
+
+def test_crowded_grid_cell(ctx):
+    # every pixel at nearly the same range and speed: all points land in one grid tile,
+    # which the work items share among many CTAs
+    r = synth.Radar(M=2, N=2, Ns=64, L=32)
+    px = synth.random_frame(r, 100, 100, seed=8, r_lo=3.0, r_hi=3.001, v_max=0.001)
+    got = ctx.synth(r, device.upload(px), "nufft").cpu().numpy()
+    ref = oracle.cube_separable(r, px)
+    assert oracle.rel_l2(got, ref) <= 2e-5
+
+
+def test_batch_equals_alone_bitwise(ctx):
+    frames = synth.walking_batch(n_frames=4, n_az=96, n_el=64)
+    radar = frames[0].radar
+    pxs = [device.upload(f) for f in frames]
+    alone = [ctx.synth(radar, px, "nufft").cpu().numpy() for px in pxs]
+    again = [ctx.synth(radar, px, "nufft").cpu().numpy() for px in pxs]
+    batch = [c.cpu().numpy() for c in ctx.synth_batch(radar, pxs, "nufft")]
+    for a, b, c in zip(alone, again, batch):
+        assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def test_empty_frame_gives_zero(ctx):
+    f = synth.config2()
+    px = f.pixels.astype(np.float32)
+    px.sigma_re[:] = 0.0
+    px.sigma_im[:] = 0.0
+    got = ctx.synth(f.radar, device.upload(px), "nufft").cpu().numpy()
+    assert np.all(got == 0)
+
+
+@pytest.mark.parametrize("Ns,L", [(4096, 4), (64, 2)])
+def test_unsupported_axes(ctx, Ns, L):
+    r = synth.Radar(M=1, N=1, Ns=Ns, L=L)
+    px = synth.random_frame(r, 8, 8, seed=1)
+    with pytest.raises(_abi.RsimError) as e:
+        ctx.synth(r, device.upload(px), "nufft")
+    assert e.value.status == _abi.ERR_UNSUPPORTED

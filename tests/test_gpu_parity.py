@@ -15,9 +15,9 @@ from paper_2307_09226_gb300.synth import Pixels, Radar
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 2e-5, "split_fp16": 2e-5, "split_bf16": 2e-5, "bf16": 1e-2, "fp16": 1e-2}
+TOL = {"fp32": 2e-5, "split_fp16": 2e-5, "split_bf16": 2e-5, "bf16": 1e-2, "fp16": 1e-2, "nufft": 2e-5}
 TENSOR_TIERS = ("split_fp16", "split_bf16", "bf16", "fp16")
-ALL_TIERS = ("fp32",) + TENSOR_TIERS
+ALL_TIERS = ("fp32",) + TENSOR_TIERS + ("nufft",)
 
 
 @pytest.fixture(scope="module")
