@@ -336,6 +336,9 @@ def run_gpu(args):
         batch = run_batch(ctx, tier, steps=max(3, min(args.steps, 10)), warmup=3) if not args.no_extras else None
         serving = run_serving(ctx) if not args.no_extras else None
         raycast = run_raycast(ctx, tier) if not args.no_extras else None
+        nufft = run_nufft(ctx, frame, px, ref, args.steps, args.warmup) if not args.no_extras else None
+        if nufft is not None:
+            nufft["speedup_vs_headline_tier"] = round(step_ms / args.steps / nufft["ms_per_step"], 3)
         line = {
             "metric": "cube synth Gpath-samples/s at rel err<=2e-5 vs FP64",
             "value": value, "unit": "Gpath-samples/s", "n_gpus": ws, "steps": args.steps,
@@ -362,6 +365,7 @@ def run_gpu(args):
             "batch": batch,
             "serving": serving,
             "raycast": raycast,
+            "nufft": nufft,
         }
         print(json.dumps(line))
     ctx.close()
@@ -442,6 +446,52 @@ def run_batch(ctx, tier, steps, warmup):
             "value": samples / (t * 1e-3) / 1e9, "unit": "Gpath-samples/s", "steps": steps,
             "doppler_time": {"ms_64_frames": round(a.elapsed_time(b), 4),
                              "e_velo_m_s": round(oracle.e_velo(vest.cpu().numpy(), truth), 4)}}
+
+
+def run_nufft(ctx, frame, px, ref, steps, warmup):
+    """The NUFFT form of the same config-2 frame (the alternative to the tensor-core
+    contraction): accuracy against the FP64 oracle, device time per frame with the L2
+    flushed between steps, the stage split, and the CPU NUFFT reference on two channels."""
+    import torch
+    import oracle
+    import oracle.nufft as nu
+    from paper_2307_09226_gb300 import _abi, device
+    radar = frame.radar
+    cube = device.cube_tensor(radar)
+    ctx.synth(radar, px, "nufft", cube=cube)
+    err = oracle.rel_l2(cube.cpu().numpy(), ref)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(warmup):
+        ctx.synth(radar, px, "nufft", cube=cube)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        ev[i][0].record()
+        ctx.synth(radar, px, "nufft", cube=cube)
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    _abi.rsim_profile_enable(ctx.h, True)
+    for i in range(steps):
+        flush.fill_(float(i))
+        ctx.synth(radar, px, "nufft", cube=cube)
+    prof = _abi.rsim_profile_read(ctx.h)
+    _abi.rsim_profile_enable(ctx.h, False)
+    pv = int(oracle.valid_mask(frame.pixels.sigma_re, frame.pixels.sigma_im).sum())
+    samples = pv * radar.V * radar.Ns * radar.L
+    t = sum(ms) / len(ms)
+    t0 = time.perf_counter()
+    nu.cube_nufft(radar, frame.pixels, w=7, channels=[0, 1])
+    cpu_s = time.perf_counter() - t0
+    return {"workload": frame.meta["workload"], "tier": "nufft", "kernel_width": 7,
+            "value": samples / (t * 1e-3) / 1e9, "unit": "Gpath-samples/s", "ms_per_step": round(t, 4),
+            "rel_err": err, "steps": steps, "gpu_launches": prof.kernels,
+            "stage_ms": {"prep": prof.prep_ms / prof.calls, "nufft": prof.contract_ms / prof.calls},
+            "speedup_vs_headline_tier": None,
+            "cpu_baseline": {"value": pv * 2 * radar.Ns * radar.L / cpu_s / 1e9, "unit": "Gpath-samples/s",
+                             "cores": 1, "kind": "oracle",
+                             "sample": "CPU NUFFT reference (numpy FP64, width 7), channels 0-1 of the frame"}}
 
 
 def run_raycast(ctx, tier, steps=10, warmup=3):

@@ -507,7 +507,7 @@ cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int o
                          (const int*)sc.items, (const int*)sc.item_bin, (const int*)sc.item_first,
                          (const NuRec*)sc.rec, sc.grid);
   if (e != cudaSuccess) return e;
-  const int log_rows = std::max(0, 12 - ilog2i(g.Gy));  // rows * Gy = 4096 complex per CTA
+  const int log_rows = std::max(0, 10 - ilog2i(g.Gy));  // rows * Gy = 1024 complex per CTA
   const int ysmem = ((1 << log_rows) * g.Gy + g.Gy / 2) * (int)sizeof(float2);
   e = cudaFuncSetAttribute(nu_fft_y, cudaFuncAttributeMaxDynamicSharedMemorySize, ysmem);
   if (e != cudaSuccess) return e;
@@ -515,7 +515,7 @@ cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int o
   e = launch_dependent(nu_fft_y, dim3((unsigned)yblocks), dim3(256), (size_t)ysmem, st, frame, g, log_rows,
                        ilog2i(g.Gy), (const long long*)sc.grid, sc.mid);
   if (e != cudaSuccess) return e;
-  const int log_cols = std::max(0, std::min(4, 13 - ilog2i(g.Gx)));  // cols * Gx <= 8192 complex per CTA
+  const int log_cols = std::max(0, std::min(2, 11 - ilog2i(g.Gx)));  // cols * Gx <= 2048 complex per CTA
   const int cols_per = 1 << log_cols;
   const int xsmem = (g.Gx * cols_per + g.Gx / 2) * (int)sizeof(float2);
   e = cudaFuncSetAttribute(nu_fft_x, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem);
