@@ -14,29 +14,28 @@
 // transform Psi_x(n') Psi_y(l'), is the cube (relative error ~1e-6 at w = 7).
 //
 // Kernels, per frame:
-//   nu_psi        1 / (Psi_x(n') Psi_y(l')) factors: one warp per mode, a 128-node
-//                 midpoint rule of Psi(k) = (w/2) int phi(z) cos(pi k w z / G) dz;
 //   nu_bin_count  each (channel, point) is binned by the 32 x 32 grid tile of its
 //                 nearest cell: a shared-memory histogram per block of one channel's
-//                 points, one global addition per (block, bin);
-//   nu_scan       exclusive scan of the bin counts (one block), and the table of
-//                 spreading work items: every bin cut into chunks of 256 records;
+//                 points, one global addition per (block, bin).  An extra row of blocks
+//                 builds the geometry's tables: 1 / (Psi_x(n') Psi_y(l')) (one warp per
+//                 mode, a 128-node midpoint rule of Psi(k) = (w/2) int phi(z) cos(pi k w z
+//                 / G) dz) and the twiddles of both FFTs.  The last counting block scans
+//                 the counts and cuts every bin into work items of 256 records;
 //   nu_bin_fill   records (x, y, q') stored bin by bin (one global reservation per
 //                 (block, bin), ranks within the block from shared memory);
-//   nu_spread     one CTA per work item adds its records' w x w taps into a
-//                 shared-memory tile with a (w - 1) / 2 halo, as fixed-point integers
-//                 (each term split in 16-bit halves summed by non-returning 32-bit
-//                 atomics), then adds the tile into the global 64-bit integer grid.
-//                 Integer sums are exact and do not depend on the order of the atomic
-//                 additions, so the result is bit-reproducible.  The work items share
-//                 the crowded tiles among many SMs: a scene fills only the part of the
-//                 grid that its ranges and speeds reach;
-//   nu_fft_y      rows of the grid: integer -> float, radix-2 inverse-sign FFT over the
-//                 slow-time axis in shared memory (a sequence's butterflies on
-//                 consecutive threads, twiddles from a shared table), only the L
-//                 centred modes kept;
-//   nu_fft_x      columns: FFT over the fast-time axis, only the N_s centred modes kept,
-//                 times the deconvolution factors, written to the cube.
+//   nu_spread     persistent CTAs take the work items in turn; a warp takes one record
+//                 at a time, lane k adding tap k of its w x w taps into a shared-memory tile
+//                 with a (w - 1) / 2 halo, as fixed-point integers (each term split in
+//                 16-bit halves summed by non-returning 32-bit atomics), then the tile is
+//                 added into the global 64-bit integer grid.  Integer sums are exact and do
+//                 not depend on the order of the atomic additions, so the result is
+//                 bit-reproducible.  The work items share the crowded tiles among many SMs:
+//                 a scene fills only the part of the grid that its ranges and speeds reach;
+//   nu_fft_y      rows of the grid: integer -> float, Stockham inverse-sign FFT over the
+//                 slow-time axis (radix-16 passes in registers, shared memory between
+//                 passes), only the L centred modes kept;
+//   nu_fft_x      columns: the same over the fast-time axis, only the N_s centred modes
+//                 kept, times the deconvolution factors, written to the cube.
 #include <math.h>
 
 #include <algorithm>
@@ -53,12 +52,23 @@ constexpr int kNTile = 32;                  // grid cells per tile side
 constexpr int kNPad = kNTile + 2 * kNHalf;  // tile side with the halo
 constexpr int kNQuad = 128;                 // midpoint nodes for Psi
 constexpr int kSpreadChunk = 256;           // records per spreading work item
-constexpr int kBinThreads = 1024;           // binning blocks: one channel, kBinItems points
+constexpr int kBinThreads = 256;            // binning blocks: one channel, kBinItems points
 constexpr int kBinItems = 4 * kBinThreads;
+static_assert(kBinThreads % 32 == 0 && kBinThreads <= 1024, "binning blocks are whole warps");
 
 struct NuRec {
   uint32_t x, y;  // positions, 2^-32 cycles
   float2 q;       // shifted strength q'
+};
+
+// FFT of length n = 2^k (16 <= n <= 4096) along one grid axis: T = n / 16 threads per
+// sequence, S sequences per CTA, each in a shared-memory buffer of `pitch` float2;
+// passes of radix 16 then one of 2, 4, 8 or 16; twiddles of pass p (p >= 1) at
+// twoff[p], radix[p] x ns[p] entries.
+struct FftPlan {
+  int n, T, S, pitch, passes;
+  int radix[3], ns[3], twoff[3];
+  int tw_size;
 };
 
 // exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1, 0 outside
@@ -106,14 +116,50 @@ __device__ __forceinline__ float grid_scale(const FrameIO& fr, bool inverse) {
 // to `hi`, so the sum is hi 2^16 + lo exactly while a word receives fewer than 2^16
 // terms (a work item holds kSpreadChunk records, each adding once per cell).
 __device__ __forceinline__ void add_split(unsigned* lo, int* hi, int v) {
-  if (v == 0) return;
   atomicAdd(lo, (unsigned)(v & 0xffff));
   atomicAdd(hi, v >> 16);
 }
 
-__global__ void nu_psi(NuGeo g, float* __restrict__ inv_x, float* __restrict__ inv_y) {
-  wait_prior_grid();
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+// Twiddle e of an FFT plan: entry j ns + k of pass p is exp(+j 2 pi j k / (ns R)).
+__device__ void plan_twiddle(const FftPlan& pl, int e, float2* __restrict__ tw) {
+  for (int p = 1; p < pl.passes; ++p) {
+    const int size = pl.radix[p] * pl.ns[p];
+    if (e < pl.twoff[p] + size) {
+      const int r = e - pl.twoff[p], j = r / pl.ns[p], k = r % pl.ns[p];
+      float sn, cs;
+      sincospif((float)(2 * j * k) / (float)size, &sn, &cs);  // exact argument: size is a power of two
+      tw[e] = make_float2(cs, sn);
+      return;
+    }
+  }
+}
+
+// Tables of one frame's geometry, in blocks of kBinThreads threads numbered vb: blocks
+// [0, psi_blocks) give the deconvolution factors (one warp per mode), the blocks after
+// them the twiddle tables of both FFT plans.
+struct NuTables {
+  int psi_blocks, blocks;
+  FftPlan plx, ply;
+  float *inv_x, *inv_y;
+  float2 *twx, *twy;
+};
+
+__device__ void table_block(const NuGeo& g, const NuTables& tb, int vb) {
+  const FftPlan& plx = tb.plx;
+  const FftPlan& ply = tb.ply;
+  float* __restrict__ inv_x = tb.inv_x;
+  float* __restrict__ inv_y = tb.inv_y;
+  if (vb >= tb.psi_blocks) {
+    const int e = (vb - tb.psi_blocks) * blockDim.x + threadIdx.x;
+    float2* __restrict__ twx = tb.twx;
+    float2* __restrict__ twy = tb.twy;
+    if (e < plx.tw_size)
+      plan_twiddle(plx, e, twx);
+    else if (e - plx.tw_size < ply.tw_size)
+      plan_twiddle(ply, e - plx.tw_size, twy);
+    return;
+  }
+  const int warp = (vb * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= g.Ns + g.L) return;
   const bool xs = warp < g.Ns;
   const int k = xs ? warp - g.sx : (warp - g.Ns) - g.sy;
@@ -133,10 +179,86 @@ __global__ void nu_psi(NuGeo g, float* __restrict__ inv_x, float* __restrict__ i
   }
 }
 
-// Binning blocks: blockIdx.y = channel, blockIdx.x = a range of kBinItems points.
+// Spreading work items of a frame: bin offsets and cursors, and the item table
+// (item_bin[i] the bin of item i, item_first[i] its first record, items[0] their number).
+struct NuItems {
+  int *off, *cursor, *items, *item_bin, *item_first;
+};
+
+// Exclusive scan of n bin counts by one block into `off` and `cursor`, and of their chunk
+// counts into the work-item table.  The counts were added by other blocks' atomics, so
+// they are read from L2.
+__device__ void scan_bins(const int* __restrict__ count, int n, const NuItems& it) {
+  __shared__ int wsum[32], wcsum[32];
+  const int nt = blockDim.x, nw = nt >> 5;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  const int per = (n + nt - 1) / nt;
+  const int b0 = min(n, t * per), b1 = min(n, b0 + per);
+  int* __restrict__ off = it.off;
+  int* __restrict__ cursor = it.cursor;
+  int* __restrict__ item_bin = it.item_bin;
+  int* __restrict__ item_first = it.item_first;
+  int s = 0, c = 0;
+  for (int b = b0; b < b1; ++b) {
+    const int k = __ldcg(count + b);
+    s += k;
+    c += (k + kSpreadChunk - 1) / kSpreadChunk;
+  }
+  // inclusive scans of the records and the chunks: within warps, then over the warp sums
+  int si = s, ci = c;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, si, o), y = __shfl_up_sync(0xffffffffu, ci, o);
+    if (lane >= o) {
+      si += x;
+      ci += y;
+    }
+  }
+  if (lane == 31) {
+    wsum[w] = si;
+    wcsum[w] = ci;
+  }
+  __syncthreads();
+  if (w == 0) {
+    int a = lane < nw ? wsum[lane] : 0, bb = lane < nw ? wcsum[lane] : 0;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int x = __shfl_up_sync(0xffffffffu, a, o), y = __shfl_up_sync(0xffffffffu, bb, o);
+      if (lane >= o) {
+        a += x;
+        bb += y;
+      }
+    }
+    wsum[lane] = a;
+    wcsum[lane] = bb;
+  }
+  __syncthreads();
+  int run = (w ? wsum[w - 1] : 0) + si - s, crun = (w ? wcsum[w - 1] : 0) + ci - c;
+  for (int b = b0; b < b1; ++b) {
+    const int k = __ldcg(count + b);
+    off[b] = run;
+    cursor[b] = run;
+    for (int q = 0; q < k; q += kSpreadChunk, ++crun) {
+      item_bin[crun] = b;
+      item_first[crun] = run + q;
+    }
+    run += k;
+  }
+  if (t == nt - 1) {
+    off[n] = wsum[nw - 1];
+    it.items[0] = wcsum[nw - 1];
+  }
+}
+
+// Binning blocks: blockIdx.y = channel, blockIdx.x = a range of kBinItems points.  The row
+// blockIdx.y = V builds the geometry's tables.  The last counting block to finish (a
+// ticket taken after its counts are visible: count[nbins]) scans the counts into the work
+// items, so no block waits for another.
 __global__ void __launch_bounds__(kBinThreads) nu_bin_count(const FrameIO* __restrict__ fp, NuGeo g,
-                                                            int* __restrict__ count) {
+                                                            int* __restrict__ count, NuTables tb, NuItems it) {
   wait_prior_grid();
+  if ((int)blockIdx.y == g.V) {
+    for (int vb = blockIdx.x; vb < tb.blocks; vb += gridDim.x) table_block(g, tb, vb);
+    return;
+  }
   extern __shared__ int hist[];  // this channel's bins
   const int nb = g.ntx * g.nty, v = blockIdx.y;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
@@ -150,48 +272,15 @@ __global__ void __launch_bounds__(kBinThreads) nu_bin_count(const FrameIO* __res
   __syncthreads();
   for (int b = threadIdx.x; b < nb; b += blockDim.x)
     if (hist[b]) atomicAdd(&count[v * nb + b], hist[b]);
-}
-
-// Exclusive scan of n bin counts (one block of 1024 threads) into `off` and `cursor`, and
-// of their chunk counts into the work-item table: item_bin[i] is the bin of item i,
-// item_first[i] its first record, items[0] the number of items.
-__global__ void __launch_bounds__(1024) nu_scan(const int* __restrict__ count, int n, int* __restrict__ off,
-                                                int* __restrict__ cursor, int* __restrict__ items,
-                                                int* __restrict__ item_bin, int* __restrict__ item_first) {
-  wait_prior_grid();
-  __shared__ int part[1024], cpart[1024];
-  const int t = threadIdx.x;
-  const int per = (n + 1023) / 1024;
-  const int b0 = min(n, t * per), b1 = min(n, b0 + per);
-  int s = 0, c = 0;
-  for (int b = b0; b < b1; ++b) {
-    s += count[b];
-    c += (count[b] + kSpreadChunk - 1) / kSpreadChunk;
-  }
-  part[t] = s;
-  cpart[t] = c;
+  __shared__ int ticket;
+  __threadfence();
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scans of the chunk sums
-    const int x = t >= o ? part[t - o] : 0, y = t >= o ? cpart[t - o] : 0;
-    __syncthreads();
-    part[t] += x;
-    cpart[t] += y;
-    __syncthreads();
-  }
-  int run = part[t] - s, crun = cpart[t] - c;
-  for (int b = b0; b < b1; ++b) {
-    off[b] = run;
-    cursor[b] = run;
-    for (int k = 0; k < count[b]; k += kSpreadChunk, ++crun) {
-      item_bin[crun] = b;
-      item_first[crun] = run + k;
-    }
-    run += count[b];
-  }
-  if (t == 1023) {
-    off[n] = part[1023];
-    items[0] = cpart[1023];
-  }
+  const int nbins = g.V * nb;
+  if (threadIdx.x == 0) ticket = atomicAdd(&count[nbins], 1);
+  __syncthreads();
+  if (ticket != (int)(gridDim.x * g.V) - 1) return;
+  __threadfence();
+  scan_bins(count, nbins, it);
 }
 
 __global__ void __launch_bounds__(kBinThreads) nu_bin_fill(const FrameIO* __restrict__ fp, NuGeo g,
@@ -238,169 +327,382 @@ __global__ void __launch_bounds__(kBinThreads) nu_bin_fill(const FrameIO* __rest
   }
 }
 
-__global__ void __launch_bounds__(256) nu_spread(const FrameIO* __restrict__ fp, NuGeo g,
-                                                 const int* __restrict__ off, const int* __restrict__ items,
-                                                 const int* __restrict__ item_bin,
-                                                 const int* __restrict__ item_first,
-                                                 const NuRec* __restrict__ rec,
-                                                 unsigned long long* __restrict__ grid) {
+// Spreading layout.  A warp takes one record at a time and lane k owns tap k = kNW jx + jy
+// (lanes 0..31, then 32..48 on a second pass).  With a tile row stride of kTileStride = 7
+// (mod 32) words, the 49 taps of a record lie on consecutive banks, so each atomic
+// instruction is one shared-memory wavefront.  The weights are computed once per record
+// (one lane per record) and staged per warp: (q'_re, q'_im) psi_x by jx, psi_y by jy.
+constexpr int kTileStride = kNW + 32 * ((kNPad - kNW + 31) / 32);
+static_assert(kTileStride % 32 == kNW && kTileStride >= kNPad, "tile row stride");
+static_assert(kNW * kNW <= 64, "two passes of 32 lanes cover the taps");
+constexpr int kTileWords = (kNPad * kTileStride + 3) / 4 * 4;  // zeroed as 16-byte words
+constexpr int kSpreadThreads = 256;
+constexpr int kSpreadWarps = kSpreadThreads / 32;
+constexpr int kSpreadBlocksPerSm = 4;  // shared memory: 2 x 2 tile arrays + the staging
+constexpr int kStageLd = 33;           // staged values of 32 records per jx (or jy), padded
+
+// Persistent CTAs take the work items in turn (their number is known on the device only).
+__global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __restrict__ fp, NuGeo g,
+                                                            const int* __restrict__ off,
+                                                            const int* __restrict__ items,
+                                                            const int* __restrict__ item_bin,
+                                                            const int* __restrict__ item_first,
+                                                            const NuRec* __restrict__ rec,
+                                                            unsigned long long* __restrict__ grid) {
   wait_prior_grid();
-  if ((int)blockIdx.x >= items[0]) return;
-  __shared__ unsigned lo[2][kNPad * kNPad];
-  __shared__ int hi[2][kNPad * kNPad];
-  const int bin = item_bin[blockIdx.x];
+  __shared__ __align__(16) unsigned lo[2][kTileWords];  // re, im: low 16 bits of each term
+  __shared__ __align__(16) int hi[2][kTileWords];       // re, im: the signed rest
+  __shared__ float2 s_ax[kSpreadWarps][kNW][kStageLd];  // scale q' psi_x(jx)
+  __shared__ float s_wy[kSpreadWarps][kNW][kStageLd];   // psi_y(jy)
+  __shared__ int s_base[kSpreadWarps][32];              // tile word of the record's first tap
+  __shared__ float2 s_zero[kStageLd];                    // weights of the lanes idle on pass 2
+  for (int i = threadIdx.x; i < kStageLd; i += blockDim.x) s_zero[i] = make_float2(0.f, 0.f);
+  const int n_items = items[0];
   const int nb = g.ntx * g.nty;
-  const int v = bin / nb, ty = (bin % nb) % g.nty, tx = (bin % nb) / g.nty;
-  const int r_begin = item_first[blockIdx.x];
-  const int r_end = min(off[bin + 1], r_begin + kSpreadChunk);
-  for (int i = threadIdx.x; i < kNPad * kNPad; i += blockDim.x) {
-    lo[0][i] = lo[1][i] = 0u;
-    hi[0][i] = hi[1][i] = 0;
-  }
-  __syncthreads();
   const float scale = grid_scale(*fp, false);
-  const int x0 = tx * g.Tx - kNHalf, y0 = ty * g.Ty - kNHalf;  // padded tile origin (cells)
-  for (int r = r_begin + threadIdx.x; r < r_end; r += blockDim.x) {
-    const NuRec q = rec[r];
-    int cx, cy;
-    float dx, dy;
-    nearest_cell(q.x, g.Gx, cx, dx);
-    nearest_cell(q.y, g.Gy, cy, dy);
-    // the nearest cell lies in this tile: local padded coordinates of the first tap
-    const int lx = cx - tx * g.Tx, ly = cy - ty * g.Ty;
-    float wx[kNW], wy[kNW];
-#pragma unroll
-    for (int j = 0; j < kNW; ++j) {
-      wx[j] = es_kernel(2.f * ((float)(j - kNHalf) - dx) / (float)kNW);
-      wy[j] = es_kernel(2.f * ((float)(j - kNHalf) - dy) / (float)kNW);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // This lane's taps on the two passes.  On the second pass the lanes past the last tap
+  // add zero (their x weights are the zero row) to their first-pass word, whose bank no
+  // active lane of that pass uses, so the pass needs no branch.
+  const int jx0 = lane / kNW, jy0 = lane % kNW;
+  const bool two = lane + 32 < kNW * kNW;
+  const int jx1 = two ? (lane + 32) / kNW : jx0, jy1 = two ? (lane + 32) % kNW : jy0;
+  const int off0 = jx0 * kTileStride + jy0, off1 = jx1 * kTileStride + jy1;
+  const float2* ax0 = s_ax[warp][jx0];
+  const float2* ax1 = two ? s_ax[warp][jx1] : s_zero;
+  const float* wy0 = s_wy[warp][jy0];
+  const float* wy1 = s_wy[warp][jy1];
+  const int* sb = s_base[warp];
+  auto pass = [&](int base, float2 a, float w, int offs) {
+    const int at = base + offs;
+    add_split(&lo[0][at], &hi[0][at], __float2int_rn(a.x * w));
+    add_split(&lo[1][at], &hi[1][at], __float2int_rn(a.y * w));
+  };
+  auto taps = [&](int r) {
+    const int base = sb[r];
+    pass(base, ax0[r], wy0[r], off0);
+    pass(base, ax1[r], wy1[r], off1);
+  };
+  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    const int bin = item_bin[item];
+    const int v = bin / nb, ty = (bin % nb) % g.nty, tx = (bin % nb) / g.nty;
+    const int r_begin = item_first[item];
+    const int r_end = min(off[bin + 1], r_begin + kSpreadChunk);
+    for (int i = threadIdx.x; i < kTileWords / 4; i += blockDim.x) {
+      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+      reinterpret_cast<uint4*>(lo[0])[i] = z;
+      reinterpret_cast<uint4*>(lo[1])[i] = z;
+      reinterpret_cast<uint4*>(hi[0])[i] = z;
+      reinterpret_cast<uint4*>(hi[1])[i] = z;
     }
-    const float qr = q.q.x * scale, qi = q.q.y * scale;
+    __syncthreads();
+    for (int r0 = r_begin + warp * 32; r0 < r_end; r0 += kSpreadThreads) {
+      const int n = min(32, r_end - r0);
+      if (lane < n) {
+        const NuRec q = rec[r0 + lane];
+        int cx, cy;
+        float dx, dy;
+        nearest_cell(q.x, g.Gx, cx, dx);
+        nearest_cell(q.y, g.Gy, cy, dy);
+        // the nearest cell lies in this tile: local padded coordinates of the first tap
+        const int lx = cx - tx * g.Tx, ly = cy - ty * g.Ty;
+        const float qr = q.q.x * scale, qi = q.q.y * scale;
 #pragma unroll
-    for (int jx = 0; jx < kNW; ++jx) {
-      const float ar = qr * wx[jx], ai = qi * wx[jx];
-      const int row = (lx + jx) * kNPad + ly;
+        for (int j = 0; j < kNW; ++j) {
+          constexpr float k2w = 2.f / (float)kNW;
+          const float wx = es_kernel(((float)(j - kNHalf) - dx) * k2w);
+          s_ax[warp][j][lane] = make_float2(qr * wx, qi * wx);
+          s_wy[warp][j][lane] = es_kernel(((float)(j - kNHalf) - dy) * k2w);
+        }
+        s_base[warp][lane] = lx * kTileStride + ly;
+      }
+      __syncwarp();
+      int r = 0;
+      for (; r + 1 < n; r += 2) {
+        taps(r);
+        taps(r + 1);
+      }
+      if (r < n) taps(r);
+      __syncwarp();
+    }
+    __syncthreads();
+    const int x0 = tx * g.Tx - kNHalf, y0 = ty * g.Ty - kNHalf;  // padded tile origin (cells)
+    const int64_t gbase = (int64_t)v * g.Gx * g.Gy;
+    for (int i = threadIdx.x; i < kNPad * kNPad; i += blockDim.x) {
+      const int row = i / kNPad, col = i % kNPad, at = row * kTileStride + col;
+      const long long re = ((long long)hi[0][at] << 16) + (long long)lo[0][at];
+      const long long im = ((long long)hi[1][at] << 16) + (long long)lo[1][at];
+      if (re == 0 && im == 0) continue;
+      const int gx = (x0 + row) & (g.Gx - 1), gy = (y0 + col) & (g.Gy - 1);
+      unsigned long long* cell = grid + 2 * (gbase + (int64_t)gx * g.Gy + gy);
+      atomicAdd(cell, (unsigned long long)re);
+      atomicAdd(cell + 1, (unsigned long long)im);
+    }
+    __syncthreads();  // the tile is read before the next item clears it
+  }
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 w) {
+  return make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
+}
+
+// exp(+j 2 pi m / 16) for 0 <= m < 8: cosines and sines of multiples of pi / 8
+__device__ __forceinline__ float2 unit16(int m) {
+  constexpr float c1 = 0.92387953251128676f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  switch (m) {
+    case 0: return make_float2(1.f, 0.f);
+    case 1: return make_float2(c1, s1);
+    case 2: return make_float2(h, h);
+    case 3: return make_float2(s1, c1);
+    case 4: return make_float2(0.f, 1.f);
+    case 5: return make_float2(-s1, c1);
+    case 6: return make_float2(-h, h);
+    default: return make_float2(-c1, s1);
+  }
+}
+
+__host__ __device__ constexpr int rev_bits(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((i >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+__host__ __device__ constexpr int log2_c(int r) { return r <= 1 ? 0 : 1 + log2_c(r >> 1); }
+
+// In-register inverse-sign DFT of R <= 16 points, natural order in and out:
+// A_m = sum_j a_j exp(+j 2 pi j m / R), by radix-2 decimation in time.
+template <int R>
+__device__ __forceinline__ void dft_inv(float2 (&a)[R]) {
+  constexpr int bits = log2_c(R);
+  float2 b[R];
 #pragma unroll
-      for (int jy = 0; jy < kNW; ++jy) {
-        add_split(&lo[0][row + jy], &hi[0][row + jy], __float2int_rn(ar * wy[jy]));
-        add_split(&lo[1][row + jy], &hi[1][row + jy], __float2int_rn(ai * wy[jy]));
+  for (int i = 0; i < R; ++i) b[rev_bits(i, bits)] = a[i];
+#pragma unroll
+  for (int h = 1; h < R; h <<= 1) {
+#pragma unroll
+    for (int i0 = 0; i0 < R; i0 += 2 * h) {
+#pragma unroll
+      for (int k = 0; k < h; ++k) {
+        const int m = k * (8 / h);  // exp(+j 2 pi k / (2 h)) = unit16(k 16 / (2 h))
+        const float2 u = b[i0 + k];
+        float2 t = b[i0 + k + h];
+        if (m == 4)
+          t = make_float2(-t.y, t.x);
+        else if (m != 0)
+          t = cmul(t, unit16(m));
+        b[i0 + k] = make_float2(u.x + t.x, u.y + t.y);
+        b[i0 + k + h] = make_float2(u.x - t.x, u.y - t.y);
       }
     }
   }
-  __syncthreads();
-  const int64_t gbase = (int64_t)v * g.Gx * g.Gy;
-  for (int i = threadIdx.x; i < kNPad * kNPad; i += blockDim.x) {
-    const long long re = ((long long)hi[0][i] << 16) + (long long)lo[0][i];
-    const long long im = ((long long)hi[1][i] << 16) + (long long)lo[1][i];
-    if (re == 0 && im == 0) continue;
-    const int gx = (x0 + i / kNPad) & (g.Gx - 1), gy = (y0 + i % kNPad) & (g.Gy - 1);
-    unsigned long long* cell = grid + 2 * (gbase + (int64_t)gx * g.Gy + gy);
-    atomicAdd(cell, (unsigned long long)re);
-    atomicAdd(cell + 1, (unsigned long long)im);
+#pragma unroll
+  for (int i = 0; i < R; ++i) a[i] = b[i];
+}
+
+// One radix-R pass of a Stockham (self-sorting) inverse-sign FFT of length n; every thread
+// holds kFftPer = 16 values, i.e. 16 / R butterflies.  Butterfly b reads inputs
+// j < R at b + j n / R, multiplies input j by exp(+j 2 pi j k / (Ns R)) with k = b mod Ns
+// (Ns the product of the earlier radices; tw[j Ns + k] holds that factor), takes the R-point
+// DFT and writes output m to (b / Ns) Ns R + k + m Ns.  After the last pass the sequence
+// is its DFT in natural order.  sync_mid: loads and stores share the buffer.
+constexpr int kFftPer = 16;
+
+template <int R, class Load, class Store>
+__device__ __forceinline__ void fft_pass(int n, int ns, int t, int T, const float2* __restrict__ tw, bool sync_mid,
+                                         Load load, Store store) {
+  constexpr int G = kFftPer / R;
+  const int nr = n / R;
+  float2 a[G][R];
+#pragma unroll
+  for (int gi = 0; gi < G; ++gi) {
+    const int b = t + gi * T;
+    const int k = b & (ns - 1);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      float2 x = load(b + j * nr);
+      if (j > 0 && ns > 1) x = cmul(x, tw[j * ns + k]);
+      a[gi][j] = x;
+    }
+    dft_inv<R>(a[gi]);
+  }
+  if (sync_mid) __syncthreads();
+#pragma unroll
+  for (int gi = 0; gi < G; ++gi) {
+    const int b = t + gi * T;
+    const int k = b & (ns - 1);
+    const int o = (b - k) * R + k;
+#pragma unroll
+    for (int m = 0; m < R; ++m) store(o + m * ns, a[gi][m]);
   }
 }
 
-// twiddles tw[k] = exp(+j 2 pi k / n) for k < n / 2, built once per CTA
-__device__ void build_twiddles(float2* tw, int n) {
-  for (int k = threadIdx.x; k < n / 2; k += blockDim.x) {
-    float sn, cs;
-    sincospif(2.f * (float)k / (float)n, &sn, &cs);
-    tw[k] = make_float2(cs, sn);
-  }
-}
-
-// In-place radix-2 inverse-sign butterflies over `count` = 2^logc sequences of length
-// n = 2^logn in shared memory, element i of sequence j at x[i * istride + j * jstride],
-// already in bit-reversed order.  CONTIG: the elements of a sequence are adjacent
-// (istride 1), so a sequence's butterflies go to consecutive threads; otherwise the
-// sequences are adjacent (jstride 1) and consecutive threads take consecutive sequences.
-// Both keep a warp's shared-memory accesses on distinct banks.
-template <bool CONTIG>
-__device__ void fft_inv_stages(float2* x, const float2* tw, int logn, int logc, int istride, int jstride) {
-  const int half_total = 1 << (logn - 1 + logc);
-  const int hmask = (1 << (logn - 1)) - 1, cmask = (1 << logc) - 1;
-  for (int s = 1; s <= logn; ++s) {
-    const int h = 1 << (s - 1);
+// All passes of one FFT per sequence, P passes (radix 16, then RL last), from the
+// sequence's input `in` (element i at in[i]) to its shared-memory buffer x (element i at
+// i + i / 16, so that the stride-16 stores of the first pass fall on distinct banks); the
+// transform ends in x, in natural order.  The buffers may overlap the input: the first pass
+// holds all its inputs in registers before the block stores anything.  Each (P, RL) is its own kernel, so that a kernel
+// holds only the passes it runs.
+template <int P, int RL, class In>
+__device__ __forceinline__ void fft_all(const FftPlan& pl, const In& in, float2* x, int t,
+                                        const float2* __restrict__ tw) {
+  static_assert(P > 1 || RL == 16, "a single pass is one radix-16 butterfly");
+  auto sload = [=](int i) -> float2 { return x[i + (i >> 4)]; };
+  auto sstore = [=](int i, float2 v) { x[i + (i >> 4)] = v; };
+  float2 a[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) a[j] = in(t + j * pl.T);
+  __syncthreads();  // the buffers overlap the input rows
+  dft_inv<16>(a);  // the first pass has Ns = 1: no twiddles, output m at 16 t + m
+#pragma unroll
+  for (int m = 0; m < 16; ++m) sstore(16 * t + m, a[m]);
+  if constexpr (P > 1) {
     __syncthreads();
-    for (int t = threadIdx.x; t < half_total; t += blockDim.x) {
-      const int b = CONTIG ? (t & hmask) : (t >> logc);
-      const int j = CONTIG ? (t >> (logn - 1)) : (t & cmask);
-      const int k = b & (h - 1);
-      const int i0 = ((b >> (s - 1)) << s) + k, i1 = i0 + h;
-      const float2 w = tw[k << (logn - s)];
-      float2* p0 = x + i0 * istride + j * jstride;
-      float2* p1 = x + i1 * istride + j * jstride;
-      const float2 u = *p0, a = *p1;
-      const float2 vv = make_float2(a.x * w.x - a.y * w.y, a.x * w.y + a.y * w.x);
-      *p0 = make_float2(u.x + vv.x, u.y + vv.y);
-      *p1 = make_float2(u.x - vv.x, u.y - vv.y);
+    if constexpr (P == 3) {
+      fft_pass<16>(pl.n, 16, t, pl.T, tw + pl.twoff[1], true, sload, sstore);
+      __syncthreads();
     }
+    fft_pass<RL>(pl.n, pl.ns[P - 1], t, pl.T, tw + pl.twoff[P - 1], true, sload, sstore);
   }
   __syncthreads();
 }
 
-__device__ __forceinline__ unsigned bitrev(unsigned x, int bits) { return __brev(x) >> (32 - bits); }
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-// Rows (v, mx) of the grid: 2^log_rows rows per CTA, FFT over my, the L centred modes kept.
-__global__ void nu_fft_y(const FrameIO* __restrict__ fp, NuGeo g, int log_rows, int ybits,
-                         const long long* __restrict__ grid, float2* __restrict__ mid) {
-  wait_prior_grid();
-  extern __shared__ float2 sy[];  // [rows][Gy], then Gy / 2 twiddles
-  const int rows_per = 1 << log_rows;
-  float2* tw = sy + rows_per * g.Gy;
-  build_twiddles(tw, g.Gy);
-  const float inv = grid_scale(*fp, true);
-  const int64_t r0 = (int64_t)blockIdx.x * rows_per;  // row = v * Gx + mx
-  const int64_t rows = (int64_t)g.V * g.Gx;
-  for (int e = threadIdx.x; e < rows_per * g.Gy; e += blockDim.x) {
-    const int rr = e >> ybits, m = e & (g.Gy - 1);
-    const int64_t row = r0 + rr;
-    float2 val = make_float2(0.f, 0.f);
-    if (row < rows) {
-      const long long* c = grid + 2 * (row * g.Gy + m);
-      val = make_float2(ll_to_float(c[0]) * inv, ll_to_float(c[1]) * inv);
-    }
-    sy[rr * g.Gy + bitrev((unsigned)m, ybits)] = val;
+constexpr unsigned long long kNuWaitNs = 2000000000ull;  // 2 s for a copy, then give up
+
+// One CTA's input rows: a single bulk copy (TMA) global -> shared of `bytes` (a multiple of
+// 16, both addresses 16-byte aligned), completing the barrier's transaction count.  Every
+// thread waits, bounded: on a timeout the status word gets kStatusTimeout and the copy is
+// waited for once more (bounded too).  The block agrees on the outcome: false, and every
+// thread returns, if any thread timed out.
+__device__ bool load_rows(void* dst, const void* src, uint32_t bytes, uint64_t* bar, unsigned* status) {
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  fft_inv_stages<true>(sy, tw, ybits, log_rows, 1, g.Gy);
-  for (int e = threadIdx.x; e < rows_per * g.L; e += blockDim.x) {
-    const int rr = e / g.L, l = e % g.L;
-    const int64_t row = r0 + rr;
-    if (row >= rows) continue;
-    mid[row * g.L + l] = sy[rr * g.Gy + ((l - g.sy) & (g.Gy - 1))];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+  }
+  bool ok = false;
+  for (int round = 0; round < 2; ++round) {
+    unsigned long long t0 = 0;
+    bool done_round = false;
+    for (uint32_t it = 0;; ++it) {
+      uint32_t done;
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}"
+          : "=r"(done)
+          : "r"(smem_addr(bar))
+          : "memory");
+      if (done) {
+        ok = round == 0;
+        done_round = true;
+        break;
+      }
+      if ((it & 255u) == 255u) {
+        unsigned long long now;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+        if (t0 == 0) {
+          t0 = now;
+        } else if (now - t0 > kNuWaitNs) {
+          if (round == 0) atomicOr(status, kStatusTimeout);
+          break;
+        }
+      }
+    }
+    if (done_round) break;
+  }
+  return !__syncthreads_or(!ok);
+}
+
+// Dynamic shared memory of an FFT kernel: the CTA's raw input rows, overlapped by the S
+// transform buffers (whichever is larger), then the copy barrier.
+__host__ __device__ inline int fft_smem_in_bytes(const FftPlan& pl, int elem) { return (pl.S * pl.n * elem + 127) / 128 * 128; }
+__host__ __device__ inline int fft_smem_bytes(const FftPlan& pl, int elem) {
+  const int buf = (pl.S * pl.pitch * 8 + 15) / 16 * 16;
+  const int in = fft_smem_in_bytes(pl, elem);
+  return (in > buf ? in : buf) + 16;
+}
+
+// Rows (v, mx) of the grid, pl.S consecutive rows per CTA, one bulk copy: integer -> float,
+// FFT over my, the L centred modes kept and written as midT[v][l][mx] (column-major rows), so
+// that the column pass reads its columns as contiguous rows.
+template <int P, int RL>
+__global__ void nu_fft_y(const FrameIO* __restrict__ fp, NuGeo g, FftPlan pl, const float2* __restrict__ tw,
+                         const long long* __restrict__ grid, float2* __restrict__ midT, unsigned* status) {
+  wait_prior_grid();
+  extern __shared__ __align__(128) unsigned char smem_y[];
+  const longlong2* raw = reinterpret_cast<const longlong2*>(smem_y);
+  float2* buf = reinterpret_cast<float2*>(smem_y);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_y + fft_smem_bytes(pl, 16) - 16);
+  const int64_t rows = (int64_t)g.V * g.Gx, row0 = (int64_t)blockIdx.x * pl.S;
+  const int live_rows = (int)min((int64_t)pl.S, rows - row0);
+  if (!load_rows(smem_y, grid + 2 * row0 * g.Gy, (uint32_t)(live_rows * g.Gy * 16), bar, status)) return;
+  const int t = threadIdx.x % pl.T, s = threadIdx.x / pl.T;
+  const float inv = grid_scale(*fp, true);
+  const longlong2* src = raw + (int64_t)s * g.Gy;
+  const bool live = s < live_rows;
+  auto in = [=](int i) -> float2 {
+    if (!live) return make_float2(0.f, 0.f);
+    const longlong2 c = src[i];
+    return make_float2(ll_to_float(c.x) * inv, ll_to_float(c.y) * inv);
+  };
+  fft_all<P, RL>(pl, in, buf + s * pl.pitch, t, tw);
+  // midT[v][l][mx]: consecutive threads take consecutive rows of one l
+  for (int e = threadIdx.x; e < pl.S * g.L; e += blockDim.x) {
+    const int rs = e % pl.S, l = e / pl.S;
+    if (rs >= live_rows) continue;
+    const int i = (l - g.sy) & (g.Gy - 1);
+    const int64_t row = row0 + rs, v = row / g.Gx, mx = row % g.Gx;
+    midT[(v * g.L + l) * g.Gx + mx] = buf[rs * pl.pitch + i + (i >> 4)];
   }
 }
 
-// Columns (v, l) of the row-transformed grid: 2^log_cols columns per CTA, FFT over mx,
-// the N_s centred modes kept, deconvolved and written to the cube.
-__global__ void nu_fft_x(const FrameIO* __restrict__ fp, NuGeo g, int log_cols, int xbits,
-                         const float2* __restrict__ mid, const float* __restrict__ inv_x,
-                         const float* __restrict__ inv_y, int out_dtype) {
+// Columns (v, l) of the row-transformed grid, pl.S columns per CTA (contiguous rows of
+// midT, one bulk copy): FFT over mx, the N_s centred modes kept, deconvolved and written
+// to the cube.
+template <int P, int RL>
+__global__ void nu_fft_x(const FrameIO* __restrict__ fp, NuGeo g, FftPlan pl, const float2* __restrict__ tw,
+                         const float2* __restrict__ midT, const float* __restrict__ inv_x,
+                         const float* __restrict__ inv_y, int out_dtype, unsigned* status) {
   wait_prior_grid();
-  extern __shared__ float2 sx[];  // [Gx][cols], then Gx / 2 twiddles
-  const int cols_per = 1 << log_cols;
-  float2* tw = sx + g.Gx * cols_per;
-  build_twiddles(tw, g.Gx);
-  const int cblocks = (g.L + cols_per - 1) / cols_per;
-  const int v = blockIdx.x / cblocks, l0 = (blockIdx.x % cblocks) * cols_per;
-  const float2* src = mid + (int64_t)v * g.Gx * g.L;
-  for (int e = threadIdx.x; e < g.Gx * cols_per; e += blockDim.x) {
-    const int m = e >> log_cols, j = e & (cols_per - 1);
-    const int l = l0 + j;
-    sx[bitrev((unsigned)m, xbits) * cols_per + j] = (l < g.L) ? src[(int64_t)m * g.L + l] : make_float2(0.f, 0.f);
-  }
-  fft_inv_stages<false>(sx, tw, xbits, log_cols, cols_per, 1);
-  const FrameIO& fr = *fp;
-  for (int e = threadIdx.x; e < g.Ns * cols_per; e += blockDim.x) {
-    const int n = e >> log_cols, j = e & (cols_per - 1);
-    const int l = l0 + j;
-    if (l >= g.L) continue;
-    const float2 s = sx[((n - g.sx) & (g.Gx - 1)) * cols_per + j];
+  extern __shared__ __align__(128) unsigned char smem_x[];
+  const float2* raw = reinterpret_cast<const float2*>(smem_x);
+  float2* buf = reinterpret_cast<float2*>(smem_x);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_x + fft_smem_bytes(pl, 8) - 16);
+  const int cblocks = (g.L + pl.S - 1) / pl.S;
+  const int v = blockIdx.x / cblocks, l0 = (blockIdx.x % cblocks) * pl.S;
+  const int live_cols = min(pl.S, g.L - l0);
+  if (!load_rows(smem_x, midT + ((int64_t)v * g.L + l0) * g.Gx, (uint32_t)(live_cols * g.Gx * 8), bar, status))
+    return;
+  const int t = threadIdx.x % pl.T, s = threadIdx.x / pl.T;
+  const float2* src = raw + (int64_t)s * g.Gx;
+  const bool live = s < live_cols;
+  auto in = [=](int i) -> float2 { return live ? src[i] : make_float2(0.f, 0.f); };
+  fft_all<P, RL>(pl, in, buf + s * pl.pitch, t, tw);
+  void* cube = fp->cube;
+  // cube[v][n][l]: consecutive threads take consecutive l of one n
+  for (int e = threadIdx.x; e < pl.S * g.Ns; e += blockDim.x) {
+    const int cs = e % pl.S, n = e / pl.S;
+    if (cs >= live_cols) continue;
+    const int i = (n - g.sx) & (g.Gx - 1), l = l0 + cs;
+    const float2 val = buf[cs * pl.pitch + i + (i >> 4)];
     const float f = inv_x[n] * inv_y[l];
     const int64_t o = ((int64_t)v * g.Ns + n) * g.L + l;
     if (out_dtype == RSIM_C128)
-      reinterpret_cast<double2*>(fr.cube)[o] = make_double2((double)(s.x * f), (double)(s.y * f));
+      reinterpret_cast<double2*>(cube)[o] = make_double2((double)(val.x * f), (double)(val.y * f));
     else
-      reinterpret_cast<float2*>(fr.cube)[o] = make_float2(s.x * f, s.y * f);
+      reinterpret_cast<float2*>(cube)[o] = make_float2(val.x * f, val.y * f);
   }
 }
 
@@ -416,6 +718,54 @@ int pow2_at_least(int x) {
   return g;
 }
 
+// A sequence's T threads are adjacent, S sequences per CTA.  The pitch puts the 16 threads
+// of a half-warp on distinct bank pairs: for T < 16 in the passes (16 / T sequences, the
+// same positions), otherwise in the write-out (S sequences read at one position).
+FftPlan fft_plan(int n) {
+  FftPlan pl{};
+  pl.n = n;
+  pl.T = n / kFftPer;
+  const int logn = ilog2i(n);
+  pl.passes = (logn + 3) / 4;
+  int ns = 1, off = 0;
+  for (int p = 0; p < pl.passes; ++p) {
+    pl.radix[p] = p + 1 < pl.passes ? 16 : 1 << (logn - 4 * (pl.passes - 1));
+    pl.ns[p] = ns;
+    pl.twoff[p] = off;
+    if (p > 0) off += pl.radix[p] * ns;
+    ns *= pl.radix[p];
+  }
+  pl.tw_size = off;
+  pl.S = std::max(1, 128 / pl.T);
+  const int target = pl.T < 16 ? pl.T : 16 / std::min(pl.S, 16);  // wanted pitch mod 16
+  const int base = n + n / 16;
+  pl.pitch = base + ((target - base % 16) % 16 + 16) % 16;
+  return pl;
+}
+
+// The kernel instantiation of a plan: passes and the radix of the last pass.
+template <template <int, int> class K>
+typename K<1, 16>::Fn pick_fft(const FftPlan& pl) {
+  const int rl = pl.radix[pl.passes - 1];
+  if (pl.passes == 1) return K<1, 16>::fn();
+  if (pl.passes == 2)
+    return rl == 16 ? K<2, 16>::fn() : rl == 8 ? K<2, 8>::fn() : rl == 4 ? K<2, 4>::fn() : K<2, 2>::fn();
+  return rl == 16 ? K<3, 16>::fn() : rl == 8 ? K<3, 8>::fn() : rl == 4 ? K<3, 4>::fn() : K<3, 2>::fn();
+}
+
+template <int P, int RL>
+struct FftY {
+  using Fn = void (*)(const FrameIO*, NuGeo, FftPlan, const float2*, const long long*, float2*, unsigned*);
+  static Fn fn() { return nu_fft_y<P, RL>; }
+};
+
+template <int P, int RL>
+struct FftX {
+  using Fn = void (*)(const FrameIO*, NuGeo, FftPlan, const float2*, const float2*, const float*, const float*, int,
+                      unsigned*);
+  static Fn fn() { return nu_fft_x<P, RL>; }
+};
+
 // Scratch of one frame: bin counts, cursors and offsets; the spreading work items; the
 // records; the 64-bit integer grid; the row-transformed grid; the deconvolution factors.
 struct NuScratch {
@@ -424,10 +774,11 @@ struct NuScratch {
   unsigned long long* grid;
   float2* mid;
   float *inv_x, *inv_y;
+  float2 *tw_x, *tw_y;
   size_t grid_bytes, total;
 };
 
-NuScratch nufft_layout(const NuGeo& g, char* base) {
+NuScratch nufft_layout(const NuGeo& g, const FftPlan& plx, const FftPlan& ply, char* base) {
   const size_t nbins = (size_t)g.V * g.ntx * g.nty;
   const size_t max_items = nbins + ((size_t)g.V * g.P + kSpreadChunk - 1) / kSpreadChunk;
   auto up = [](size_t b) { return (b + 255) / 256 * 256; };
@@ -438,7 +789,7 @@ NuScratch nufft_layout(const NuGeo& g, char* base) {
     o += up(bytes);
     return p;
   };
-  sc.count = (int*)take(4 * nbins);
+  sc.count = (int*)take(4 * (nbins + 1));  // the bin counts, then the finished-block count
   sc.cursor = (int*)take(4 * nbins);
   sc.off = (int*)take(4 * (nbins + 1));
   sc.items = (int*)take(4);
@@ -450,6 +801,8 @@ NuScratch nufft_layout(const NuGeo& g, char* base) {
   sc.mid = (float2*)take(8 * (size_t)g.V * g.Gx * g.L);
   sc.inv_x = (float*)take(4 * (size_t)(g.Ns + g.L));
   sc.inv_y = sc.inv_x ? sc.inv_x + g.Ns : nullptr;
+  sc.tw_x = (float2*)take(8 * (size_t)(plx.tw_size + ply.tw_size + 1));
+  sc.tw_y = sc.tw_x ? sc.tw_x + plx.tw_size : nullptr;
   sc.total = o;
   return sc;
 }
@@ -461,8 +814,8 @@ NuGeo nufft_geometry(const Consts& k, int64_t P) {
   g.V = k.V;
   g.Ns = k.Ns;
   g.L = k.L;
-  g.Gx = pow2_at_least(2 * k.Ns);
-  g.Gy = pow2_at_least(2 * k.L);
+  g.Gx = std::max(16, pow2_at_least(2 * k.Ns));  // at least one radix-16 FFT pass
+  g.Gy = std::max(16, pow2_at_least(2 * k.L));
   g.Tx = std::min(kNTile, g.Gx);
   g.Ty = std::min(kNTile, g.Gy);
   g.ntx = g.Gx / g.Tx;
@@ -478,52 +831,66 @@ bool nufft_supported(const Consts& k) {
   return 2 * (int64_t)k.Ns <= 4096 && 2 * (int64_t)k.L <= 4096 && k.Ns >= 4 && k.L >= 4;
 }
 
-size_t nufft_scratch_bytes(const Consts& k, int64_t P) { return nufft_layout(nufft_geometry(k, P), nullptr).total; }
+size_t nufft_scratch_bytes(const Consts& k, int64_t P) {
+  const NuGeo g = nufft_geometry(k, P);
+  return nufft_layout(g, fft_plan(g.Gx), fft_plan(g.Gy), nullptr).total;
+}
 
 cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int out_dtype, char* scratch,
-                         cudaStream_t st) {
+                         unsigned* status, cudaStream_t st) {
   const NuGeo g = nufft_geometry(k, P);
   const int nb = g.ntx * g.nty;
   const int nbins = g.V * nb;
   const int64_t max_items = nbins + ((int64_t)g.V * g.P + kSpreadChunk - 1) / kSpreadChunk;
-  const NuScratch sc = nufft_layout(g, scratch);
-  cudaError_t e = cudaMemsetAsync(sc.count, 0, 4 * (size_t)nbins, st);
+  const FftPlan plx = fft_plan(g.Gx), ply = fft_plan(g.Gy);
+  const NuScratch sc = nufft_layout(g, plx, ply, scratch);
+  int dev = 0, num_sms = 0;
+  cudaError_t e0 = cudaGetDevice(&dev);
+  if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e0 != cudaSuccess) return e0;
+  cudaError_t e = cudaMemsetAsync(sc.count, 0, 4 * ((size_t)nbins + 1), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sc.grid, 0, sc.grid_bytes, st);
   if (e != cudaSuccess) return e;
   const dim3 bgrid((unsigned)((g.P + kBinItems - 1) / kBinItems), (unsigned)g.V);
   e = cudaFuncSetAttribute(nu_bin_count, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * nb);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(nu_bin_fill, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 * nb);
   if (e != cudaSuccess) return e;
-  e = launch_dependent(nu_psi, dim3((unsigned)((g.Ns + g.L + 7) / 8)), dim3(256), 0, st, g, sc.inv_x, sc.inv_y);
-  if (e == cudaSuccess)
-    e = launch_dependent(nu_bin_count, bgrid, dim3(kBinThreads), (size_t)(4 * nb), st, frame, g, sc.count);
-  if (e == cudaSuccess)
-    e = launch_dependent(nu_scan, dim3(1), dim3(1024), 0, st, (const int*)sc.count, nbins, sc.off, sc.cursor,
-                         sc.items, sc.item_bin, sc.item_first);
+  NuTables tb{};
+  tb.psi_blocks = (g.Ns + g.L + kBinThreads / 32 - 1) / (kBinThreads / 32);
+  tb.blocks = tb.psi_blocks + (plx.tw_size + ply.tw_size + kBinThreads - 1) / kBinThreads;
+  tb.plx = plx;
+  tb.ply = ply;
+  tb.inv_x = sc.inv_x;
+  tb.inv_y = sc.inv_y;
+  tb.twx = sc.tw_x;
+  tb.twy = sc.tw_y;
+  const NuItems it{sc.off, sc.cursor, sc.items, sc.item_bin, sc.item_first};
+  e = launch_dependent(nu_bin_count, dim3(bgrid.x, bgrid.y + 1), dim3(kBinThreads), (size_t)(4 * nb), st, frame, g,
+                       sc.count, tb, it);
   if (e == cudaSuccess)
     e = launch_dependent(nu_bin_fill, bgrid, dim3(kBinThreads), (size_t)(8 * nb), st, frame, g, sc.cursor, sc.rec);
   if (e == cudaSuccess)
-    e = launch_dependent(nu_spread, dim3((unsigned)max_items), dim3(256), 0, st, frame, g, (const int*)sc.off,
+    e = launch_dependent(nu_spread, dim3((unsigned)std::min<int64_t>(max_items, kSpreadBlocksPerSm * num_sms)),
+                         dim3(kSpreadThreads), 0, st, frame, g, (const int*)sc.off,
                          (const int*)sc.items, (const int*)sc.item_bin, (const int*)sc.item_first,
                          (const NuRec*)sc.rec, sc.grid);
   if (e != cudaSuccess) return e;
-  const int log_rows = std::max(0, 10 - ilog2i(g.Gy));  // rows * Gy = 1024 complex per CTA
-  const int ysmem = ((1 << log_rows) * g.Gy + g.Gy / 2) * (int)sizeof(float2);
-  e = cudaFuncSetAttribute(nu_fft_y, cudaFuncAttributeMaxDynamicSharedMemorySize, ysmem);
+  const int ysmem = fft_smem_bytes(ply, 16);
+  const auto fft_y = pick_fft<FftY>(ply);
+  e = cudaFuncSetAttribute(fft_y, cudaFuncAttributeMaxDynamicSharedMemorySize, ysmem);
   if (e != cudaSuccess) return e;
-  const int64_t yblocks = ((int64_t)g.V * g.Gx + (1 << log_rows) - 1) >> log_rows;
-  e = launch_dependent(nu_fft_y, dim3((unsigned)yblocks), dim3(256), (size_t)ysmem, st, frame, g, log_rows,
-                       ilog2i(g.Gy), (const long long*)sc.grid, sc.mid);
+  const int64_t yblocks = ((int64_t)g.V * g.Gx + ply.S - 1) / ply.S;
+  e = launch_dependent(fft_y, dim3((unsigned)yblocks), dim3((unsigned)(ply.S * ply.T)), (size_t)ysmem, st, frame,
+                       g, ply, (const float2*)sc.tw_y, (const long long*)sc.grid, sc.mid, status);
   if (e != cudaSuccess) return e;
-  const int log_cols = std::max(0, std::min(2, 11 - ilog2i(g.Gx)));  // cols * Gx <= 2048 complex per CTA
-  const int cols_per = 1 << log_cols;
-  const int xsmem = (g.Gx * cols_per + g.Gx / 2) * (int)sizeof(float2);
-  e = cudaFuncSetAttribute(nu_fft_x, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem);
+  const int xsmem = fft_smem_bytes(plx, 8);
+  const auto fft_x = pick_fft<FftX>(plx);
+  e = cudaFuncSetAttribute(fft_x, cudaFuncAttributeMaxDynamicSharedMemorySize, xsmem);
   if (e != cudaSuccess) return e;
-  const int xblocks = g.V * ((g.L + cols_per - 1) / cols_per);
-  return launch_dependent(nu_fft_x, dim3((unsigned)xblocks), dim3(256), (size_t)xsmem, st, frame, g, log_cols,
-                          ilog2i(g.Gx), (const float2*)sc.mid, (const float*)sc.inv_x, (const float*)sc.inv_y,
-                          out_dtype);
+  const int xblocks = g.V * ((g.L + plx.S - 1) / plx.S);
+  return launch_dependent(fft_x, dim3((unsigned)xblocks), dim3((unsigned)(plx.S * plx.T)), (size_t)xsmem, st,
+                          frame, g, plx, (const float2*)sc.tw_x, (const float2*)sc.mid, (const float*)sc.inv_x,
+                          (const float*)sc.inv_y, out_dtype, status);
 }
 
 }  // namespace rsim

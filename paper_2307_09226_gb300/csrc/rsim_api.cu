@@ -272,10 +272,10 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     for (int i = 0; i < kProfEvents; ++i) ev[i] = ctx->ev_pool[base + i];
     ctx->prof_calls++;
     // compaction + phases (2); FP32: direct sum (1); tensor tiers: operand builder (1 when
-    // a frame has valid pixels), frame order (1 for a batch), contraction (1); the split
-    // reduction (1 when the partial buffer is used)
+    // a frame has valid pixels), frame order (1 for a batch), contraction (1); NUFFT: the
+    // NUFFT kernels of each frame; the split reduction (1 when the partial buffer is used)
     const bool tensor = tensor_tier(tier);
-    ctx->prof_kernels += 2 + (tier == RSIM_TIER_NUFFT ? 7 * F
+    ctx->prof_kernels += 2 + (tier == RSIM_TIER_NUFFT ? kNufftKernels * F
                               : tensor ? 1 + (mp > 0 ? 1 : 0) + (F > 1 ? 1 : 0) : 1) + (use_partial ? 1 : 0);
     cudaEventRecord(ev[0], st);
   }
@@ -288,7 +288,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     if (!nufft_supported(k)) return fail(RSIM_ERR_UNSUPPORTED, "the NUFFT tier needs N_s and L in 4..2048");
     char* scratch = ws + align_up(frames_bytes(k, Ps.data(), F, splits, tier), 256);
     for (int f = 0; f < F; ++f) {
-      e = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch, st);
+      e = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch, status, st);
       if (e != cudaSuccess) return cuda_fail(e, "NUFFT kernels");
     }
     if (prof) cudaEventRecord(ev[2], st);

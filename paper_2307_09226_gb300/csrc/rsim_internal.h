@@ -86,13 +86,17 @@ struct NuGeo {
   int sx, sy;     // centring shifts Ns / 2, L / 2
   int64_t P;      // pixel bound (items per channel)
 };
+// Kernels launch_nufft starts per frame (binning with the tables and the scan, record
+// fill, spreading, two FFT passes).
+constexpr int kNufftKernels = 5;
 NuGeo nufft_geometry(const Consts& k, int64_t P);
 bool nufft_supported(const Consts& k);
 size_t nufft_scratch_bytes(const Consts& k, int64_t P);
 // One frame (`frame`: device pointer to its table entry, P: its pixel count), using
-// nufft_scratch_bytes(k, P) bytes of scratch.
+// nufft_scratch_bytes(k, P) bytes of scratch; a copy that times out sets kStatusTimeout in
+// `status`.
 cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int out_dtype, char* scratch,
-                         cudaStream_t st);
+                         unsigned* status, cudaStream_t st);
 
 // Programmatic dependent launch: a kernel launched with launch_dependent may be
 // scheduled while the previous kernel in the stream drains its last blocks, hiding the
