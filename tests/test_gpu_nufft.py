@@ -61,6 +61,18 @@ def test_empty_frame_gives_zero(ctx):
     assert np.all(got == 0)
 
 
+# Grid sides G = 2 N from 16 to 4096 take every FFT kernel shape: one radix-16 pass
+# (G = 16), radix 16 then 2, 4, 8 or 16 (G = 32 .. 256), and two radix-16 passes then
+# 2, 4, 8 or 16 (G = 512 .. 4096), on both axes; G = 4096 is the largest grid supported.
+@pytest.mark.parametrize("Ns,L", [(8, 2048), (16, 1024), (32, 512), (64, 256), (128, 128), (256, 64),
+                                  (512, 32), (1024, 16), (2048, 8)])
+def test_every_fft_shape_against_exact_sum(ctx, Ns, L):
+    f = synth.parity_frame(seed=Ns + L, M=1, N=2, Ns=Ns, L=L, n_az=13, n_el=11)
+    got = ctx.synth(f.radar, device.upload(f), "nufft").cpu().numpy()
+    ref = oracle.cube_separable(f.radar, f.pixels)
+    assert oracle.rel_l2(got, ref) <= 2e-5
+
+
 @pytest.mark.parametrize("Ns,L", [(4096, 4), (64, 2)])
 def test_unsupported_axes(ctx, Ns, L):
     r = synth.Radar(M=1, N=1, Ns=Ns, L=L)
