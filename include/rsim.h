@@ -294,6 +294,16 @@ rsim_status rsim_raycast(rsim_ctx* ctx, const rsim_camera* cam, const rsim_primi
  * RSIM_OK, RSIM_ERR_NONFINITE or RSIM_ERR_TIMEOUT. */
 rsim_status rsim_sync_status(rsim_ctx* ctx, rsim_stream stream);
 
+/* Failure-detection self test (no counterpart in the paper: it checks the library's own
+ * safeguard).  Every device-side wait in the library gives up after a time limit,
+ * records RSIM_ERR_TIMEOUT in the context's status word and returns instead of hanging.
+ * This call enqueues one small kernel that runs that bounded wait on a barrier phase
+ * that nothing completes, with a limit of limit_ns nanoseconds (1e3 .. 1e10); the
+ * kernel returns after about that long, and rsim_sync_status() then reports
+ * RSIM_ERR_TIMEOUT once.  The context stays usable.  Asynchronous on `stream`.
+ * Errors: INVALID_ARG (NULL ctx, limit out of range), CUDA. */
+rsim_status rsim_selftest_wait_timeout(rsim_ctx* ctx, uint64_t limit_ns, rsim_stream stream);
+
 /* Stage timing for benchmarks.  While profiling is on, every rsim_synth /
  * rsim_synth_batch call records CUDA events on its stream around its three stages
  * (compaction + FP64 phases, contraction, split reduction), and on the tensor-core

@@ -123,6 +123,7 @@ SIGNATURES = {
     "rsim_range_doppler": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(c_void_p), c_int32,
                                    c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "rsim_sync_status": (c_int, [c_void_p, c_void_p]),
+    "rsim_selftest_wait_timeout": (c_int, [c_void_p, c_uint64, c_void_p]),
     "rsim_autotune": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
                               POINTER(rsim_plan), c_void_p]),
     "rsim_raycast": (c_int, [c_void_p, POINTER(rsim_camera), POINTER(rsim_primitive), c_int32,
@@ -290,6 +291,10 @@ def rsim_range_doppler(ctx, radar, cubes, power, v_est, peak=None, skip_static=F
 def rsim_sync_status(ctx, stream=None) -> int:
     """Returns the status code (does not raise) so callers can test for NONFINITE."""
     return int(load().rsim_sync_status(ctx, _stream(stream)))
+
+
+def rsim_selftest_wait_timeout(ctx, limit_ns: int, stream=None) -> None:
+    check(load().rsim_selftest_wait_timeout(ctx, int(limit_ns), _stream(stream)))
 
 
 def rsim_autotune(ctx, radar, P: int, tier: int, stream=None) -> rsim_plan:

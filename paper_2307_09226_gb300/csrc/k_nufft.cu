@@ -576,10 +576,7 @@ constexpr unsigned long long kNuWaitNs = 2000000000ull;  // 2 s for a copy, then
 // waited for once more (bounded too).  The block agrees on the outcome: false, and every
 // thread returns, if any thread timed out.
 __device__ bool load_rows(void* dst, const void* src, uint32_t bytes, uint64_t* bar, unsigned* status) {
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
+  if (threadIdx.x == 0) mbar_init_single(bar);
   __syncthreads();
   if (threadIdx.x == 0) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
@@ -592,35 +589,10 @@ __device__ bool load_rows(void* dst, const void* src, uint32_t bytes, uint64_t* 
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
   }
-  bool ok = false;
-  for (int round = 0; round < 2; ++round) {
-    unsigned long long t0 = 0;
-    bool done_round = false;
-    for (uint32_t it = 0;; ++it) {
-      uint32_t done;
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}"
-          : "=r"(done)
-          : "r"(smem_addr(bar))
-          : "memory");
-      if (done) {
-        ok = round == 0;
-        done_round = true;
-        break;
-      }
-      if ((it & 255u) == 255u) {
-        unsigned long long now;
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
-        if (t0 == 0) {
-          t0 = now;
-        } else if (now - t0 > kNuWaitNs) {
-          if (round == 0) atomicOr(status, kStatusTimeout);
-          break;
-        }
-      }
-    }
-    if (done_round) break;
+  bool ok = wait_phase_bounded(bar, 0, kNuWaitNs);
+  if (!ok) {
+    atomicOr(status, kStatusTimeout);
+    wait_phase_bounded(bar, 0, kNuWaitNs);  // the copy may still be in flight
   }
   return !__syncthreads_or(!ok);
 }

@@ -506,6 +506,16 @@ rsim_status rsim_sync_status(rsim_ctx* ctx, rsim_stream stream) {
   return RSIM_OK;
 }
 
+rsim_status rsim_selftest_wait_timeout(rsim_ctx* ctx, uint64_t limit_ns, rsim_stream stream) {
+  if (!ctx) return fail(RSIM_ERR_INVALID_ARG, "ctx is NULL");
+  if (limit_ns < 1000ull || limit_ns > 10000000000ull)
+    return fail(RSIM_ERR_INVALID_ARG, "limit_ns must lie in [1 us, 10 s]");
+  cudaSetDevice(ctx->device);
+  const cudaError_t e = launch_wait_selftest(ctx->status_dev, limit_ns, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "self-test kernel");
+  return RSIM_OK;
+}
+
 rsim_status rsim_profile_enable(rsim_ctx* ctx, int32_t on) {
   if (!ctx) return fail(RSIM_ERR_INVALID_ARG, "ctx is NULL");
   ctx->prof = on != 0;

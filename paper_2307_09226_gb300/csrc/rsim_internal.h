@@ -106,6 +106,44 @@ cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int o
 // a kernel launched without the attribute).
 __device__ __forceinline__ void wait_prior_grid() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// Shared-memory mbarrier with one expected arrival, initialised by the calling thread;
+// the block synchronises before any other thread uses it.
+__device__ __forceinline__ void mbar_init_single(uint64_t* bar) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(a) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Bounded wait for the phase of parity `parity` of the shared-memory mbarrier `bar`: polls
+// with try_wait and reads %globaltimer every 256 polls.  True once the phase has
+// completed, false when limit_ns passed first (the caller records the timeout).
+__device__ __forceinline__ bool wait_phase_bounded(uint64_t* bar, uint32_t parity, unsigned long long limit_ns) {
+  const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((it & 255u) == 255u) {
+      unsigned long long now;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(now));
+      if (t0 == 0)
+        t0 = now;
+      else if (now - t0 > limit_ns)
+        return false;
+    }
+  }
+}
+
+// Failure-detection self test: one CTA waits (wait_phase_bounded) on a barrier phase that
+// nothing completes and, after limit_ns, sets kStatusTimeout in `status`.
+cudaError_t launch_wait_selftest(unsigned* status, unsigned long long limit_ns, cudaStream_t st);
+
 template <typename... KArgs, typename... Args>
 cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
                              Args&&... args) {

@@ -95,3 +95,8 @@ class Context:
 
     def sync_status(self, stream=None) -> int:
         return _abi.rsim_sync_status(self.h, stream)
+
+    def selftest_wait_timeout(self, limit_ns: int, stream=None) -> None:
+        """Run the library's bounded device wait on a barrier nothing completes; the
+        next sync_status() reports the timeout."""
+        _abi.rsim_selftest_wait_timeout(self.h, limit_ns, stream)
