@@ -149,6 +149,20 @@ rsim_status rsim_workspace_size(rsim_ctx* ctx, const rsim_radar_params* params, 
 rsim_status rsim_synth(rsim_ctx* ctx, const rsim_radar_params* params, const rsim_pixels* pixels,
                        rsim_tier tier, void* cube, int32_t out_dtype, rsim_stream stream);
 
+/* rsim_synth on HOST buffers, for callers whose render buffers live in host memory
+ * and who want the cube back there.  The six pixel arrays (`pixels`) and `cube`
+ * ([M*N][Ns][L] complex64 or complex128) are HOST pointers.  The call copies the pixel
+ * arrays into a device staging buffer owned by the context (one cudaMemcpyAsync per
+ * array), synthesises the cube there exactly as rsim_synth does, and copies it back
+ * (one cudaMemcpyAsync), all on `stream`.  The host buffers must stay valid and
+ * unchanged until the stream has passed the copies (e.g. rsim_sync_status); with
+ * page-locked host memory the copies are asynchronous, with pageable memory they block
+ * the calling thread.  The staging buffer grows when needed (cudaMalloc after one
+ * stream synchronisation) and counts against the context's budget with the workspace.
+ * Errors: as rsim_synth. */
+rsim_status rsim_synth_host(rsim_ctx* ctx, const rsim_radar_params* params, const rsim_pixels* pixels,
+                            rsim_tier tier, void* cube, int32_t out_dtype, rsim_stream stream);
+
 /* Synthesise F frames that share one radar configuration in one pass: one launch
  * per stage over all frames, the contraction as one persistent launch whose work
  * units (frame, row tile, column tile, pixel split) are taken from a device

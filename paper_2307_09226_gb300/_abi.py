@@ -113,6 +113,8 @@ SIGNATURES = {
                                     POINTER(c_size_t)]),
     "rsim_synth": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels), c_int,
                            c_void_p, c_int32, c_void_p]),
+    "rsim_synth_host": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels), c_int,
+                           c_void_p, c_int32, c_void_p]),
     "rsim_synth_batch": (c_int, [c_void_p, POINTER(rsim_radar_params), POINTER(rsim_pixels),
                                  c_int32, POINTER(c_void_p), c_int, c_int32, c_void_p]),
     "rsim_synth_static": (c_int, [POINTER(rsim_radar_params), POINTER(rsim_pixels), c_int, c_void_p,
@@ -242,6 +244,19 @@ def rsim_synth(ctx, radar, pixels, tier: int, cube, stream=None):
     px = pixels if isinstance(pixels, rsim_pixels) else pixels_struct(pixels)
     check(load().rsim_synth(ctx, ctypes.byref(radar_params(radar)), ctypes.byref(px), int(tier),
                             _ptr(cube), od, _stream(stream)))
+
+
+def rsim_synth_host(ctx, radar, pixels, tier: int, cube, stream=None):
+    """pixels: six equal-length contiguous HOST tensors (page-locked for asynchronous
+    copies); cube: contiguous complex64/complex128 HOST tensor [M*N, Ns, L]."""
+    import torch
+    if cube.device.type != "cpu" or any(pixels[k].device.type != "cpu" for k in pixels):
+        raise ValueError("rsim_synth_host takes host tensors")
+    od = C128 if cube.dtype == torch.complex128 else C64
+    if cube.dtype not in (torch.complex64, torch.complex128) or not cube.is_contiguous():
+        raise ValueError("cube must be a contiguous complex64/complex128 tensor")
+    check(load().rsim_synth_host(ctx, ctypes.byref(radar_params(radar)), ctypes.byref(pixels_struct(pixels)),
+                                 int(tier), _ptr(cube), od, _stream(stream)))
 
 
 def rsim_synth_batch(ctx, radar, frames, tier: int, cubes, stream=None):

@@ -361,6 +361,7 @@ rsim_status rsim_destroy(rsim_ctx* ctx) {
   cudaSetDevice(ctx->device);
   cudaDeviceSynchronize();
   if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->status_dev) cudaFree(ctx->status_dev);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
   delete ctx;
@@ -384,6 +385,58 @@ rsim_status rsim_synth(rsim_ctx* ctx, const rsim_radar_params* params, const rsi
                        rsim_tier tier, void* cube, int32_t out_dtype, rsim_stream stream) {
   void* cubes[1] = {cube};
   return rsim_synth_batch(ctx, params, pixels, 1, cubes, tier, out_dtype, stream);
+}
+
+rsim_status rsim_synth_host(rsim_ctx* ctx, const rsim_radar_params* params, const rsim_pixels* pixels,
+                            rsim_tier tier, void* cube, int32_t out_dtype, rsim_stream stream) {
+  if (!ctx) return fail(RSIM_ERR_INVALID_ARG, "ctx is NULL");
+  if (!cube) return fail(RSIM_ERR_INVALID_ARG, "cube is NULL");
+  if (out_dtype != RSIM_C64 && out_dtype != RSIM_C128)
+    return fail(RSIM_ERR_INVALID_ARG, "out_dtype must be RSIM_C64 or RSIM_C128");
+  Consts k;
+  rsim_status s = check_params(params, &k);
+  if (s != RSIM_OK) return s;
+  s = check_pixels(pixels);
+  if (s != RSIM_OK) return s;
+  const size_t elem = pixels->dtype == RSIM_F64 ? 8 : 4;
+  const size_t arr = align_up((size_t)pixels->P * elem, 256);
+  const size_t cube_bytes = (size_t)k.V * (size_t)k.Ns * (size_t)k.L * (out_dtype == RSIM_C128 ? 16 : 8);
+  const size_t need = 6 * arr + cube_bytes;
+  cudaError_t e = cudaSetDevice(ctx->device);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (ctx->stage_bytes < need) {
+    if (ctx->budget && ctx->ws_bytes + need > ctx->budget)
+      return fail(RSIM_ERR_BUDGET, "staging of " + std::to_string(need) + " bytes exceeds the context budget");
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    if (ctx->stage) cudaFree(ctx->stage);
+    ctx->stage = nullptr;
+    ctx->stage_bytes = 0;
+    e = cudaMalloc(&ctx->stage, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(RSIM_ERR_OOM, "cudaMalloc of the staging buffer (" + std::to_string(need) + " bytes) failed");
+    }
+    ctx->stage_bytes = need;
+  }
+  char* base = (char*)ctx->stage;
+  const void* src[6] = {pixels->range, pixels->sigma_re, pixels->sigma_im, pixels->az, pixels->el, pixels->vel};
+  rsim_pixels dev = *pixels;
+  const void** dst[6] = {&dev.range, &dev.sigma_re, &dev.sigma_im, &dev.az, &dev.el, &dev.vel};
+  for (int i = 0; i < 6; ++i) {
+    *dst[i] = base + i * arr;
+    if (pixels->P > 0) {
+      e = cudaMemcpyAsync(base + i * arr, src[i], (size_t)pixels->P * elem, cudaMemcpyHostToDevice, st);
+      if (e != cudaSuccess) return cuda_fail(e, "copy of a pixel array to the device");
+    }
+  }
+  void* cube_dev = base + 6 * arr;
+  s = rsim_synth(ctx, params, &dev, tier, cube_dev, out_dtype, stream);
+  if (s != RSIM_OK) return s;
+  e = cudaMemcpyAsync(cube, cube_dev, cube_bytes, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return cuda_fail(e, "copy of the cube to the host");
+  return RSIM_OK;
 }
 
 rsim_status rsim_synth_batch(rsim_ctx* ctx, const rsim_radar_params* params,

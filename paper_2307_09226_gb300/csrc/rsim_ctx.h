@@ -20,6 +20,8 @@ struct rsim_ctx {
   void* ws = nullptr;
   size_t ws_bytes = 0;
   unsigned* status_dev = nullptr;
+  void* stage = nullptr;  // rsim_synth_host: device copies of the pixel arrays and the cube
+  size_t stage_bytes = 0;
   std::mutex plan_mu;
   std::map<std::string, rsim_plan> plans;
   // stage profiling (rsim_profile_enable / rsim_profile_read)

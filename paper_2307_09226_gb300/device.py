@@ -54,6 +54,15 @@ class Context:
         _abi.rsim_synth(self.h, radar, pixels, t, cube, stream)
         return cube
 
+    def synth_host(self, radar, pixels, tier="fp32", cube=None, out_dtype="complex64", stream=None):
+        """synth on host tensors: the library copies the pixels in and the cube out on
+        `stream`; the cube is complete after a synchronisation."""
+        t = _abi.TIERS[tier] if isinstance(tier, str) else int(tier)
+        if cube is None:
+            cube = cube_tensor(radar, out_dtype, device="cpu").pin_memory()
+        _abi.rsim_synth_host(self.h, radar, pixels, t, cube, stream)
+        return cube
+
     def synth_batch(self, radar, frames, tier="fp32", cubes=None, out_dtype="complex64", stream=None):
         t = _abi.TIERS[tier] if isinstance(tier, str) else int(tier)
         if cubes is None:
