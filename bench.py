@@ -128,6 +128,39 @@ def _peaks():
             "sm_max_mhz": 2070.0}, "fallback"
 
 
+def _cpu_model():
+    """The host CPU's model name (lscpu), else the machine type."""
+    import platform
+    import subprocess
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.machine()
+
+
+def _cpu_one_core(frame):
+    """The oracle on one host core: channel 0 of the frame in a child process whose BLAS
+    and OpenMP pools hold one thread.  Returns (path-samples/s, sample, seconds)."""
+    import subprocess
+    import oracle
+    r = frame.radar
+    pv = int(oracle.valid_mask(frame.pixels.sigma_re, frame.pixels.sigma_im).sum())
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle; from paper_2307_09226_gb300 import synth; "
+            "f = synth.config2(); t = time.perf_counter(); oracle.cube_separable(f.radar, f.pixels, channels=[0]); "
+            "print(time.perf_counter() - t)" % ROOT)
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=300)
+        dt = float(out.stdout.strip().splitlines()[-1])
+    except Exception:
+        return None, None, None
+    return pv * r.Ns * r.L / dt, f"1 of {r.V} channels x all {pv} valid pixels x {r.Ns}x{r.L}", dt
+
+
 def _roofline(tier, prof_contract_ms, launches, samples, peaks, peak_kind):
     """Roofline of the contraction kernel (its own CUDA-event time, without the operand
     builder): algorithmic work is 8 real flops (one complex MAC) per path-sample."""
@@ -330,6 +363,7 @@ def run_gpu(args):
         if traffic is not None:
             roof["traffic"] = traffic
         cpu_v, cores, sample, _ = _cpu_sample(frame) if ws == 1 or rank == 0 else (None, None, None, None)
+        one_v, one_sample, _ = _cpu_one_core(frame)
         batch = run_batch(ctx, tier, steps=max(3, min(args.steps, 10)), warmup=3) if not args.no_extras else None
         serving = run_serving(ctx) if not args.no_extras else None
         raycast = run_raycast(ctx, tier) if not args.no_extras else None
@@ -355,7 +389,11 @@ def run_gpu(args):
             "gpu_launches": prof.kernels,
             "roofline": roof,
             "cpu_baseline": {"value": cpu_v / 1e9, "unit": "Gpath-samples/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample, "cpu_model": _cpu_model(),
+                             "host_cores": os.cpu_count(),
+                             "one_core": None if one_v is None else
+                             {"value": one_v / 1e9, "unit": "Gpath-samples/s", "sample": one_sample}},
+            "cube_write_gbs": round(radar.V * radar.Ns * radar.L * 8 / (step_ms / args.steps * 1e-3) / 1e9, 2),
             "e2e": {"value": e2e_value, "unit": "Gpath-samples/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "clocks": clocks,
@@ -454,6 +492,7 @@ def run_nufft(ctx, frame, px, ref, steps, warmup):
     import oracle.nufft as nu
     from paper_2307_09226_gb300 import _abi, device
     radar = frame.radar
+    pv = int(oracle.valid_mask(frame.pixels.sigma_re, frame.pixels.sigma_im).sum())
     cube = device.cube_tensor(radar)
     ctx.synth(radar, px, "nufft", cube=cube)
     err = oracle.rel_l2(cube.cpu().numpy(), ref)
@@ -475,16 +514,31 @@ def run_nufft(ctx, frame, px, ref, steps, warmup):
         ctx.synth(radar, px, "nufft", cube=cube)
     prof = _abi.rsim_profile_read(ctx.h)
     _abi.rsim_profile_enable(ctx.h, False)
-    pv = int(oracle.valid_mask(frame.pixels.sigma_re, frame.pixels.sigma_im).sum())
     samples = pv * radar.V * radar.Ns * radar.L
     t = sum(ms) / len(ms)
+    # spreading (the dominant kernel): 49 taps x (re, im) x two 16-bit halves = 196 shared
+    # atomic lane-operations per (channel, point) record, against one 32-lane shared
+    # wavefront per clock per SM
+    spread_ms = prof.main_ms / prof.calls
+    lane_ops = 196.0 * radar.V * pv
+    peaks, _ = _peaks()
+    clk = peaks.get("sm_max_mhz", 2070.0)
+    peak = 152 * 32 * clk * 1e6 / 1e12
+    achieved = lane_ops / (spread_ms * 1e-3) / 1e12
+    roof = {"bound": "smem", "kernel": "nu_spread", "achieved": round(achieved, 3), "peak": round(peak, 3),
+            "unit": "T lane-op/s", "frac": round(achieved / peak, 4), "kernel_ms": round(spread_ms, 5),
+            "peak_source": f"shared memory: 152 SM x 32 lanes x {clk:.0f} MHz",
+            "algorithmic": "196 shared atomic lane-operations per (channel, point) record"}
     t0 = time.perf_counter()
     nu.cube_nufft(radar, frame.pixels, w=7, channels=[0, 1])
     cpu_s = time.perf_counter() - t0
     return {"workload": frame.meta["workload"], "tier": "nufft", "kernel_width": 7,
             "value": samples / (t * 1e-3) / 1e9, "unit": "Gpath-samples/s", "ms_per_step": round(t, 4),
             "rel_err": err, "steps": steps, "gpu_launches": prof.kernels,
-            "stage_ms": {"prep": prof.prep_ms / prof.calls, "nufft": prof.contract_ms / prof.calls},
+            "stage_ms": {"prep": prof.prep_ms / prof.calls, "nufft": prof.contract_ms / prof.calls,
+                         "binning": prof.operand_ms / prof.calls, "spreading": spread_ms,
+                         "ffts": (prof.contract_ms - prof.operand_ms) / prof.calls - spread_ms},
+            "roofline": roof,
             "speedup_vs_headline_tier": None,
             "cpu_baseline": {"value": pv * 2 * radar.Ns * radar.L / cpu_s / 1e9, "unit": "Gpath-samples/s",
                              "cores": 1, "kind": "oracle",

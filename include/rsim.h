@@ -320,8 +320,9 @@ rsim_status rsim_selftest_wait_timeout(rsim_ctx* ctx, uint64_t limit_ns, rsim_st
 
 /* Stage timing for benchmarks.  While profiling is on, every rsim_synth /
  * rsim_synth_batch call records CUDA events on its stream around its three stages
- * (compaction + FP64 phases, contraction, split reduction), and on the tensor-core
- * tiers between the operand-builder kernel and the contraction kernel.  The events
+ * (compaction + FP64 phases, contraction, split reduction), and around the main kernel
+ * of the contraction stage: the tensor-core contraction (after the operand builder),
+ * the FP32 direct sum, or the NUFFT tier's spreading kernel (first frame of a batch).  The events
  * stand between the stages' kernels, so profiled calls do not overlap one stage's
  * launch with the previous stage's end.  rsim_profile_read waits for the recorded
  * events, returns the summed stage times and launch counts since profiling was
@@ -332,7 +333,9 @@ typedef struct {
   double prep_ms;           /* summed device time of the compaction + phase kernels */
   double contract_ms;       /* summed device time of the contraction kernel */
   double reduce_ms;         /* summed device time of the split reduction (0 if none) */
-  double operand_ms;        /* part of contract_ms spent in the operand builder (tensor tiers) */
+  double operand_ms;        /* part of contract_ms before the main kernel: the operand builder
+                               (tensor tiers), binning (NUFFT tier) */
+  double main_ms;           /* the main kernel: contraction, direct sum, or NUFFT spreading */
 } rsim_profile;
 
 rsim_status rsim_profile_enable(rsim_ctx* ctx, int32_t on);

@@ -100,7 +100,8 @@ class rsim_server_stats(Structure):
 
 class rsim_profile(Structure):
     _fields_ = [("calls", c_int32), ("kernels", c_int32), ("prep_ms", c_double),
-                ("contract_ms", c_double), ("reduce_ms", c_double), ("operand_ms", c_double)]
+                ("contract_ms", c_double), ("reduce_ms", c_double), ("operand_ms", c_double),
+                ("main_ms", c_double)]
 
 
 # name -> (restype, argtypes); the full exported surface of include/rsim.h

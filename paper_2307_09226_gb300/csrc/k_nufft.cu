@@ -809,7 +809,7 @@ size_t nufft_scratch_bytes(const Consts& k, int64_t P) {
 }
 
 cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int out_dtype, char* scratch,
-                         unsigned* status, cudaStream_t st) {
+                         unsigned* status, cudaStream_t st, cudaEvent_t spread_begin, cudaEvent_t spread_end) {
   const NuGeo g = nufft_geometry(k, P);
   const int nb = g.ntx * g.nty;
   const int nbins = g.V * nb;
@@ -841,11 +841,13 @@ cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int o
                        sc.count, tb, it);
   if (e == cudaSuccess)
     e = launch_dependent(nu_bin_fill, bgrid, dim3(kBinThreads), (size_t)(8 * nb), st, frame, g, sc.cursor, sc.rec);
+  if (e == cudaSuccess && spread_begin) e = cudaEventRecord(spread_begin, st);
   if (e == cudaSuccess)
     e = launch_dependent(nu_spread, dim3((unsigned)std::min<int64_t>(max_items, kSpreadBlocksPerSm * num_sms)),
                          dim3(kSpreadThreads), 0, st, frame, g, (const int*)sc.off,
                          (const int*)sc.items, (const int*)sc.item_bin, (const int*)sc.item_first,
                          (const NuRec*)sc.rec, sc.grid);
+  if (e == cudaSuccess && spread_end) e = cudaEventRecord(spread_end, st);
   if (e != cudaSuccess) return e;
   const int ysmem = fft_smem_bytes(ply, 16);
   const auto fft_y = pick_fft<FftY>(ply);

@@ -284,11 +284,12 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (prof) cudaEventRecord(ev[1], st);
   if (tier == RSIM_TIER_NUFFT) {
-    if (prof) cudaEventRecord(ev[4], st);
     if (!nufft_supported(k)) return fail(RSIM_ERR_UNSUPPORTED, "the NUFFT tier needs N_s and L in 4..2048");
     char* scratch = ws + align_up(frames_bytes(k, Ps.data(), F, splits, tier), 256);
     for (int f = 0; f < F; ++f) {
-      e = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch, status, st);
+      // the first frame's spreading kernel is bracketed by ev[4] and ev[5]
+      e = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch, status, st, prof && f == 0 ? ev[4] : nullptr,
+                       prof && f == 0 ? ev[5] : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "NUFFT kernels");
     }
     if (prof) cudaEventRecord(ev[2], st);
@@ -297,6 +298,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     e = launch_direct(k, table, F, splits, out_dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
     if (prof) cudaEventRecord(ev[2], st);
+    if (prof) cudaEventRecord(ev[5], st);
     if (use_partial) {
       e = launch_reduce(k, table, F, splits, out_dtype, 0.f, st);
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
@@ -307,6 +309,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     if (prof) cudaEventRecord(ev[2], st);
+    if (prof) cudaEventRecord(ev[5], st);
     if (use_partial) {
       const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
       e = launch_reduce_tiles(k, table, F, splits, out_dtype, scaled, ctx->num_sms, st);
@@ -587,15 +590,17 @@ rsim_status rsim_profile_read(rsim_ctx* ctx, rsim_profile* out) {
     cudaEvent_t* ev = &ctx->ev_pool[kProfEvents * (size_t)c];
     cudaError_t e = cudaEventSynchronize(ev[3]);
     if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
-    float a = 0, b = 0, d = 0, o = 0;
+    float a = 0, b = 0, d = 0, o = 0, m = 0;
     cudaEventElapsedTime(&a, ev[0], ev[1]);
     cudaEventElapsedTime(&b, ev[1], ev[2]);
     cudaEventElapsedTime(&d, ev[2], ev[3]);
     cudaEventElapsedTime(&o, ev[1], ev[4]);
+    cudaEventElapsedTime(&m, ev[4], ev[5]);
     p.prep_ms += a;
     p.contract_ms += b;
     p.reduce_ms += d;
     p.operand_ms += o;
+    p.main_ms += m;
   }
   ctx->prof_calls = 0;
   ctx->prof_kernels = 0;

@@ -10,7 +10,7 @@
 #include "rsim_internal.h"
 
 // CUDA events a profiled synth call records (stage boundaries).
-constexpr int kProfEvents = 5;
+constexpr int kProfEvents = 6;
 
 struct rsim_ctx {
   int device = 0;

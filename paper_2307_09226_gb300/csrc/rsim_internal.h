@@ -94,9 +94,10 @@ bool nufft_supported(const Consts& k);
 size_t nufft_scratch_bytes(const Consts& k, int64_t P);
 // One frame (`frame`: device pointer to its table entry, P: its pixel count), using
 // nufft_scratch_bytes(k, P) bytes of scratch; a copy that times out sets kStatusTimeout in
-// `status`.
+// `status`.  Non-null events are recorded just before and after the spreading kernel.
 cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int out_dtype, char* scratch,
-                         unsigned* status, cudaStream_t st);
+                         unsigned* status, cudaStream_t st, cudaEvent_t spread_begin = nullptr,
+                         cudaEvent_t spread_end = nullptr);
 
 // Programmatic dependent launch: a kernel launched with launch_dependent may be
 // scheduled while the previous kernel in the stream drains its last blocks, hiding the

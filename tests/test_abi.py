@@ -50,7 +50,7 @@ def test_struct_layouts_match_header():
     assert ctypes.sizeof(_abi.rsim_pixels) == 16 + 6 * 8
     assert _abi.rsim_pixels.range.offset == 16
     assert ctypes.sizeof(_abi.rsim_plan) == 32
-    assert ctypes.sizeof(_abi.rsim_profile) == 8 + 4 * 8
+    assert ctypes.sizeof(_abi.rsim_profile) == 8 + 5 * 8
     assert ctypes.sizeof(_abi.rsim_primitive) == 8 + 6 * 24 + 8
     assert _abi.PRIM_DTYPE.itemsize == ctypes.sizeof(_abi.rsim_primitive)
     for name, _ in _abi.rsim_primitive._fields_:
