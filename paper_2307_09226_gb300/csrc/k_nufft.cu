@@ -198,11 +198,20 @@ __device__ void scan_bins(const int* __restrict__ count, int n, const NuItems& i
   int* __restrict__ cursor = it.cursor;
   int* __restrict__ item_bin = it.item_bin;
   int* __restrict__ item_first = it.item_first;
+  // counts in batches of 8 loads issued together (the first batch kept for the second pass)
+  constexpr int kBatch = 8;
+  int first[kBatch];
   int s = 0, c = 0;
-  for (int b = b0; b < b1; ++b) {
-    const int k = __ldcg(count + b);
-    s += k;
-    c += (k + kSpreadChunk - 1) / kSpreadChunk;
+  for (int b = b0; b < b1; b += kBatch) {
+    int kk[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) kk[j] = b + j < b1 ? __ldcg(count + b + j) : 0;
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      s += kk[j];
+      c += (kk[j] + kSpreadChunk - 1) / kSpreadChunk;
+      if (b == b0) first[j] = kk[j];
+    }
   }
   // inclusive scans of the records and the chunks: within warps, then over the warp sums
   int si = s, ci = c;
@@ -232,15 +241,21 @@ __device__ void scan_bins(const int* __restrict__ count, int n, const NuItems& i
   }
   __syncthreads();
   int run = (w ? wsum[w - 1] : 0) + si - s, crun = (w ? wcsum[w - 1] : 0) + ci - c;
-  for (int b = b0; b < b1; ++b) {
-    const int k = __ldcg(count + b);
-    off[b] = run;
-    cursor[b] = run;
-    for (int q = 0; q < k; q += kSpreadChunk, ++crun) {
-      item_bin[crun] = b;
-      item_first[crun] = run + q;
+  for (int b = b0; b < b1; b += kBatch) {
+    int kk[kBatch];
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) kk[j] = b == b0 ? first[j] : (b + j < b1 ? __ldcg(count + b + j) : 0);
+#pragma unroll
+    for (int j = 0; j < kBatch; ++j) {
+      if (b + j >= b1) break;
+      off[b + j] = run;
+      cursor[b + j] = run;
+      for (int q = 0; q < kk[j]; q += kSpreadChunk, ++crun) {
+        item_bin[crun] = b + j;
+        item_first[crun] = run + q;
+      }
+      run += kk[j];
     }
-    run += k;
   }
   if (t == nt - 1) {
     off[n] = wsum[nw - 1];
@@ -295,6 +310,18 @@ __global__ void __launch_bounds__(kBinThreads) nu_bin_fill(const FrameIO* __rest
   const int64_t pv = (int64_t)fr.meta[0];
   const int64_t p0 = (int64_t)blockIdx.x * kBinItems;
   constexpr int kPer = kBinItems / kBinThreads;
+  // this thread's points: every load issued before the first use
+  uint32_t xq[kPer], yq[kPer], cq[kPer];
+  float2 sg[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const int64_t p = p0 + threadIdx.x + (int64_t)i * blockDim.x;
+    const bool in = p < pv;
+    xq[i] = in ? fr.phA[(int64_t)v * fr.Pcap + p] : 0u;
+    yq[i] = in ? fr.phB[p] : 0u;
+    cq[i] = in ? fr.phC[(int64_t)v * fr.Pcap + p] : 0u;
+    sg[i] = in ? fr.sig[p] : make_float2(0.f, 0.f);
+  }
   int bins[kPer], rank[kPer];
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
@@ -302,9 +329,18 @@ __global__ void __launch_bounds__(kBinThreads) nu_bin_fill(const FrameIO* __rest
     bins[i] = -1;
     rank[i] = 0;
     if (p < pv) {
-      bins[i] = bin_of(fr.phA[(int64_t)v * fr.Pcap + p], fr.phB[p], g);
+      bins[i] = bin_of(xq[i], yq[i], g);
       rank[i] = atomicAdd(&hist[bins[i]], 1);
     }
+  }
+  // q' = sigma exp(j 2 pi (c + x s_x + y s_y)), the phase exact mod 1 in 2^-32 cycles
+  float2 q[kPer];
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    const uint32_t ph = cq[i] + xq[i] * (uint32_t)g.sx + yq[i] * (uint32_t)g.sy;
+    float sn, cs;
+    sincospif((float)(int32_t)ph * 4.656612873077393e-10f, &sn, &cs);  // angle pi ph / 2^31
+    q[i] = make_float2(sg[i].x * cs - sg[i].y * sn, sg[i].x * sn + sg[i].y * cs);
   }
   __syncthreads();
   for (int b = threadIdx.x; b < nb; b += blockDim.x) base[b] = hist[b] ? atomicAdd(&cursor[v * nb + b], hist[b]) : 0;
@@ -312,17 +348,10 @@ __global__ void __launch_bounds__(kBinThreads) nu_bin_fill(const FrameIO* __rest
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
     if (bins[i] < 0) continue;
-    const int64_t p = p0 + threadIdx.x + (int64_t)i * blockDim.x;
-    const uint32_t xq = fr.phA[(int64_t)v * fr.Pcap + p], yq = fr.phB[p];
-    // q' = sigma exp(j 2 pi (c + x s_x + y s_y)), the phase exact mod 1 in 2^-32 cycles
-    const uint32_t ph = fr.phC[(int64_t)v * fr.Pcap + p] + xq * (uint32_t)g.sx + yq * (uint32_t)g.sy;
-    float sn, cs;
-    sincospif((float)(int32_t)ph * 4.656612873077393e-10f, &sn, &cs);  // angle pi ph / 2^31
-    const float2 sg = fr.sig[p];
     NuRec r;
-    r.x = xq;
-    r.y = yq;
-    r.q = make_float2(sg.x * cs - sg.y * sn, sg.x * sn + sg.y * cs);
+    r.x = xq[i];
+    r.y = yq[i];
+    r.q = q[i];
     rec[base[bins[i]] + rank[i]] = r;
   }
 }
