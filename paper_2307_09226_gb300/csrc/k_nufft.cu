@@ -377,7 +377,8 @@ __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __res
                                                             const int* __restrict__ item_bin,
                                                             const int* __restrict__ item_first,
                                                             const NuRec* __restrict__ rec,
-                                                            unsigned long long* __restrict__ grid) {
+                                                            unsigned long long* __restrict__ grid,
+                                                            int* __restrict__ row_used) {
   wait_prior_grid();
   __shared__ __align__(16) unsigned lo[2][kTileWords];  // re, im: low 16 bits of each term
   __shared__ __align__(16) int hi[2][kTileWords];       // re, im: the signed rest
@@ -417,6 +418,10 @@ __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __res
     const int v = bin / nb, ty = (bin % nb) % g.nty, tx = (bin % nb) / g.nty;
     const int r_begin = item_first[item];
     const int r_end = min(off[bin + 1], r_begin + kSpreadChunk);
+    // the grid rows this item adds to (the padded tile's, mod G_x): the row pass skips
+    // rows that no item marks, which hold zeros only
+    for (int r = threadIdx.x; r < kNPad; r += blockDim.x)
+      row_used[(int64_t)v * g.Gx + ((tx * g.Tx - kNHalf + r) & (g.Gx - 1))] = 1;
     for (int i = threadIdx.x; i < kTileWords / 4; i += blockDim.x) {
       const uint4 z = make_uint4(0u, 0u, 0u, 0u);
       reinterpret_cast<uint4*>(lo[0])[i] = z;
@@ -640,7 +645,8 @@ __host__ __device__ inline int fft_smem_bytes(const FftPlan& pl, int elem) {
 // that the column pass reads its columns as contiguous rows.
 template <int P, int RL>
 __global__ void nu_fft_y(const FrameIO* __restrict__ fp, NuGeo g, FftPlan pl, const float2* __restrict__ tw,
-                         const long long* __restrict__ grid, float2* __restrict__ midT, unsigned* status) {
+                         const long long* __restrict__ grid, float2* __restrict__ midT,
+                         const int* __restrict__ row_used, unsigned* status) {
   wait_prior_grid();
   extern __shared__ __align__(128) unsigned char smem_y[];
   const longlong2* raw = reinterpret_cast<const longlong2*>(smem_y);
@@ -648,6 +654,16 @@ __global__ void nu_fft_y(const FrameIO* __restrict__ fp, NuGeo g, FftPlan pl, co
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_y + fft_smem_bytes(pl, 16) - 16);
   const int64_t rows = (int64_t)g.V * g.Gx, row0 = (int64_t)blockIdx.x * pl.S;
   const int live_rows = (int)min((int64_t)pl.S, rows - row0);
+  // rows no spreading item touched are zero, and so is their transform: no copy, no FFT
+  if (!__syncthreads_or((int)threadIdx.x < live_rows && row_used[row0 + threadIdx.x] != 0)) {
+    for (int e = threadIdx.x; e < pl.S * g.L; e += blockDim.x) {
+      const int rs = e % pl.S, l = e / pl.S;
+      if (rs >= live_rows) continue;
+      const int64_t row = row0 + rs, v = row / g.Gx, mx = row % g.Gx;
+      midT[(v * g.L + l) * g.Gx + mx] = make_float2(0.f, 0.f);
+    }
+    return;
+  }
   if (!load_rows(smem_y, grid + 2 * row0 * g.Gy, (uint32_t)(live_rows * g.Gy * 16), bar, status)) return;
   const int t = threadIdx.x % pl.T, s = threadIdx.x / pl.T;
   const float inv = grid_scale(*fp, true);
@@ -756,7 +772,8 @@ typename K<1, 16>::Fn pick_fft(const FftPlan& pl) {
 
 template <int P, int RL>
 struct FftY {
-  using Fn = void (*)(const FrameIO*, NuGeo, FftPlan, const float2*, const long long*, float2*, unsigned*);
+  using Fn = void (*)(const FrameIO*, NuGeo, FftPlan, const float2*, const long long*, float2*, const int*,
+                      unsigned*);
   static Fn fn() { return nu_fft_y<P, RL>; }
 };
 
@@ -770,7 +787,7 @@ struct FftX {
 // Scratch of one frame: bin counts, cursors and offsets; the spreading work items; the
 // records; the 64-bit integer grid; the row-transformed grid; the deconvolution factors.
 struct NuScratch {
-  int *count, *cursor, *off, *items, *item_bin, *item_first;
+  int *count, *row_used, *cursor, *off, *items, *item_bin, *item_first;
   NuRec* rec;
   unsigned long long* grid;
   float2* mid;
@@ -790,7 +807,9 @@ NuScratch nufft_layout(const NuGeo& g, const FftPlan& plx, const FftPlan& ply, c
     o += up(bytes);
     return p;
   };
-  sc.count = (int*)take(4 * (nbins + 1));  // the bin counts, then the finished-block count
+  // the bin counts, the finished-block count, the grid rows in use (cleared together)
+  sc.count = (int*)take(4 * (nbins + 1 + (size_t)g.V * g.Gx));
+  sc.row_used = sc.count ? sc.count + nbins + 1 : nullptr;
   sc.cursor = (int*)take(4 * nbins);
   sc.off = (int*)take(4 * (nbins + 1));
   sc.items = (int*)take(4);
@@ -849,7 +868,7 @@ cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int o
   cudaError_t e0 = cudaGetDevice(&dev);
   if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev);
   if (e0 != cudaSuccess) return e0;
-  cudaError_t e = cudaMemsetAsync(sc.count, 0, 4 * ((size_t)nbins + 1), st);
+  cudaError_t e = cudaMemsetAsync(sc.count, 0, 4 * ((size_t)nbins + 1 + (size_t)g.V * g.Gx), st);
   if (e == cudaSuccess) e = cudaMemsetAsync(sc.grid, 0, sc.grid_bytes, st);
   if (e != cudaSuccess) return e;
   const dim3 bgrid((unsigned)((g.P + kBinItems - 1) / kBinItems), (unsigned)g.V);
@@ -875,7 +894,7 @@ cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int o
     e = launch_dependent(nu_spread, dim3((unsigned)std::min<int64_t>(max_items, kSpreadBlocksPerSm * num_sms)),
                          dim3(kSpreadThreads), 0, st, frame, g, (const int*)sc.off,
                          (const int*)sc.items, (const int*)sc.item_bin, (const int*)sc.item_first,
-                         (const NuRec*)sc.rec, sc.grid);
+                         (const NuRec*)sc.rec, sc.grid, sc.row_used);
   if (e == cudaSuccess && spread_end) e = cudaEventRecord(spread_end, st);
   if (e != cudaSuccess) return e;
   const int ysmem = fft_smem_bytes(ply, 16);
@@ -884,7 +903,8 @@ cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int o
   if (e != cudaSuccess) return e;
   const int64_t yblocks = ((int64_t)g.V * g.Gx + ply.S - 1) / ply.S;
   e = launch_dependent(fft_y, dim3((unsigned)yblocks), dim3((unsigned)(ply.S * ply.T)), (size_t)ysmem, st, frame,
-                       g, ply, (const float2*)sc.tw_y, (const long long*)sc.grid, sc.mid, status);
+                       g, ply, (const float2*)sc.tw_y, (const long long*)sc.grid, sc.mid, (const int*)sc.row_used,
+                       status);
   if (e != cudaSuccess) return e;
   const int xsmem = fft_smem_bytes(plx, 8);
   const auto fft_x = pick_fft<FftX>(plx);

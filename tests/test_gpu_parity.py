@@ -156,13 +156,14 @@ def test_config2_full_frame(ctx, tier):
     assert err <= TOL[tier]
 
 
-def test_full_size_serving_corner_sampled(ctx):
-    """Largest serving shape (512x512 pixels, V=48, Ns=512, L=256), FP32 tier, checked
-    at sampled entries computed one by one by the oracle."""
+@pytest.mark.parametrize("tier", ["fp32", "split_bf16", "nufft"])
+def test_full_size_serving_corner_sampled(ctx, tier):
+    """Largest serving shape (512x512 pixels, V=48, Ns=512, L=256), checked at sampled
+    entries computed one by one by the oracle."""
     radar = Radar(M=4, N=12, Ns=512, L=256)
     px = synth.random_frame(radar, 512, 512, seed=77, mask_frac=0.3)
     f = synth.Frame(radar, px, "complex64")
-    got = _run(ctx, f, "fp32")
+    got = _run(ctx, f, tier)
     rng = np.random.default_rng(5)
     ent = np.stack([rng.integers(0, 48, 24), rng.integers(0, 512, 24), rng.integers(0, 256, 24)], 1)
     want = oracle.cube_entries(radar, px, ent)
