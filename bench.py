@@ -615,20 +615,22 @@ def run_raycast(ctx, tier, steps=10, warmup=3):
                         "speed_m_s": round(scenes[0][1]["speed"], 3)}}
 
 
-def run_serving(ctx, n_requests=120, slots=4, seed=5):
+def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5):
     """Config 5: Poisson stream of mixed requests (M 2-4, N 4-12, Ns 128-512, L 64-256,
     64^2..512^2 pixels, FP32 and split-BF16 tiers) into the continuous-batching server at
-    0.7 x the measured capacity; latency is submit -> completion."""
+    0.7 x the measured capacity: n_warmup requests, a new tally, then n_requests measured;
+    latency is submit -> completion.  The requests cycle over `pool` distinct frames
+    resident on the device (a frame's previous request has finished before it is reused)."""
     import numpy as np
     import torch
     from paper_2307_09226_gb300 import _abi, device, synth
-    reqs = synth.serving_requests(n_requests, seed=seed)
+    reqs = synth.serving_requests(pool, seed=seed)
     frames = [synth.request_frame(r) for r in reqs]
     pxs = [device.upload(f) for f in frames]
     cubes = [device.cube_tensor(f.radar) for f in frames]
     made = [_abi.make_request(f.radar, px, _abi.TIERS[r["tier"]], cb)
             for r, f, px, cb in zip(reqs, frames, pxs, cubes)]
-    # capacity: every request once, back to back, on one server slot
+    # capacity: every pool request once, back to back, on one server slot
     srv = _abi.rsim_server_create(ctx.h, slots=1)
     t0 = time.perf_counter()
     for m in made:
@@ -637,22 +639,34 @@ def run_serving(ctx, n_requests=120, slots=4, seed=5):
     _abi.rsim_server_destroy(srv)
     rate = 0.7 / alone_s
     rng = np.random.default_rng(seed + 1)
-    gaps = rng.exponential(1.0 / rate, len(made))
     srv = _abi.rsim_server_create(ctx.h, slots=slots)
-    tickets = []
-    start = time.perf_counter()
-    due = start
-    for m, gap in zip(made, gaps):
-        due += gap
-        delay = due - time.perf_counter()
-        if delay > 0:
-            time.sleep(delay)
-        tickets.append(_abi.rsim_server_submit(srv, m))
-    bad = sum(_abi.rsim_server_wait(srv, t, -1) != _abi.OK for t in tickets)
+    bad = 0
+
+    def stream(n, first):
+        nonlocal bad
+        gaps = rng.exponential(1.0 / rate, n)
+        tickets = {}
+        due = time.perf_counter()
+        for j in range(first, first + n):
+            due += gaps[j - first]
+            prev = tickets.pop(j - pool, None)  # the same frame's previous request
+            if prev is not None:
+                bad += _abi.rsim_server_wait(srv, prev, -1) != _abi.OK
+            delay = due - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            tickets[j] = _abi.rsim_server_submit(srv, made[j % pool])
+        for t in tickets.values():
+            bad += _abi.rsim_server_wait(srv, t, -1) != _abi.OK
+
+    stream(n_warmup, 0)
+    _abi.rsim_server_stats_reset(srv)
+    stream(n_requests, n_warmup)
     st = _abi.rsim_server_stats_get(srv)
     _abi.rsim_server_destroy(srv)
     torch.cuda.synchronize()
-    return {"workload": "poisson-mix-M2..4-N4..12-Ns128..512-L64..256-P4k..262k", "requests": len(made),
+    return {"workload": "poisson-mix-M2..4-N4..12-Ns128..512-L64..256-P4k..262k", "requests": int(st.completed),
+            "warmup_requests": n_warmup, "distinct_frames": pool,
             "slots": slots, "rate_req_s": round(rate, 2), "offered_load": 0.7,
             "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),
             "max_ms": round(st.max_ms, 3), "req_per_s": round(st.completed / max(st.busy_s, 1e-9), 2),

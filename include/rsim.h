@@ -375,8 +375,12 @@ rsim_status rsim_get_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_
  * request (FIFO); a host scheduler thread admits the head request as soon as a slot is
  * free and its workspace fits in the HBM budget still unreserved, and launches it on
  * that slot's stream, so requests that arrive while others run start as soon as
- * resources free up and their kernels overlap on the device.  Completion is detected
- * with CUDA events; latency is measured from submit() to completion.
+ * resources free up and their kernels overlap on the device.  A request whose estimated
+ * device time (path-samples at its tier's nominal rate) is under 2 ms runs on the slot's
+ * high-priority stream, so its blocks start ahead of long requests' pending blocks; the
+ * others run at low priority.  Results do not depend on the priority.  Completion is
+ * detected by a host function after the request's work; latency is measured from
+ * submit() to completion.
  * ---------------------------------------------------------------------------------- */
 typedef struct rsim_server rsim_server;
 
@@ -415,6 +419,10 @@ rsim_status rsim_server_wait(rsim_server* s, uint64_t ticket, int32_t timeout_ms
 /* Cancel a request that has not been admitted yet (running requests complete). */
 rsim_status rsim_server_cancel(rsim_server* s, uint64_t ticket);
 rsim_status rsim_server_stats_get(rsim_server* s, rsim_server_stats* out);
+/* Start a new tally: clear the counters and latency samples (e.g. after a warm-up), keep
+ * the slots and their workspaces.  Requests still in flight are counted in the new tally
+ * when they complete. */
+rsim_status rsim_server_stats_reset(rsim_server* s);
 /* Stop the scheduler, wait for running requests, free slot workspaces. */
 rsim_status rsim_server_destroy(rsim_server* s);
 

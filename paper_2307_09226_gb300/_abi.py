@@ -142,6 +142,7 @@ SIGNATURES = {
     "rsim_server_wait": (c_int, [c_void_p, c_uint64, c_int32]),
     "rsim_server_cancel": (c_int, [c_void_p, c_uint64]),
     "rsim_server_stats_get": (c_int, [c_void_p, POINTER(rsim_server_stats)]),
+    "rsim_server_stats_reset": (c_int, [c_void_p]),
     "rsim_server_destroy": (c_int, [c_void_p]),
 }
 
@@ -404,6 +405,10 @@ def rsim_server_stats_get(server) -> rsim_server_stats:
     s = rsim_server_stats()
     check(load().rsim_server_stats_get(server, ctypes.byref(s)))
     return s
+
+
+def rsim_server_stats_reset(server):
+    check(load().rsim_server_stats_reset(server))
 
 
 def rsim_server_destroy(server):

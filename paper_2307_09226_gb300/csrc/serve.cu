@@ -1,8 +1,13 @@
 // Serving loop: continuous batching of cube-synthesis requests.
 //
-// Each slot owns a CUDA stream and a status word.  A scheduler thread admits the
-// head of the FIFO queue as soon as a slot is free and the request's workspace fits
-// in the part of the HBM budget that running requests have not reserved.  The
+// Each slot owns two CUDA streams, of the highest and the lowest priority, and a status
+// word.  A scheduler thread admits the head of the FIFO queue as soon as a slot is free
+// and the request's workspace fits in the part of the HBM budget that running requests
+// have not reserved.  A request whose estimated device time is short runs on the
+// high-priority stream: when long requests' kernels hold the SMs, the block scheduler
+// starts its blocks as soon as any resources free up instead of after the long kernels'
+// remaining blocks.  (Measured on the mixed serving workload: p50 and p99 both lower than
+// with one priority; a third, middle level lowered p50 further but raised p99.)  The
 // workspace comes from the stream-ordered allocator on the slot's stream and goes
 // back to it when the request completes, so memory frees up in launch order.  Work
 // of different slots overlaps on the device.  Completion is reported by a host
@@ -41,11 +46,14 @@ struct Req {
   rsim_status result = RSIM_OK;
   Clock::time_point t_submit, t_done;
   int slot = -1;
+  int prio = 0;  // index into the slot's streams: 0 high priority, 1 low
   void* ws = nullptr;
 };
 
+constexpr int kPrios = 2;
+
 struct Slot {
-  cudaStream_t st = nullptr;
+  cudaStream_t st[kPrios] = {};         // highest priority first
   unsigned* status = nullptr;           // device status word of this slot
   unsigned long long* pv_host = nullptr;  // pinned: P_valid of the request in flight
   uint64_t ticket = 0;
@@ -109,7 +117,7 @@ void retire(rsim_server* s, int si) {
   if (it != s->reqs.end()) {
     Req& r = it->second;
     r.t_done = Clock::now();
-    if (r.ws) cudaFreeAsync(r.ws, sl.st);
+    if (r.ws) cudaFreeAsync(r.ws, sl.st[r.prio]);
     r.ws = nullptr;
     s->reserved -= r.bytes;
     if (e != cudaSuccess) r.result = RSIM_ERR_CUDA;
@@ -145,7 +153,8 @@ bool admit_one(rsim_server* s) {
   if (s->opts.hbm_budget_bytes && s->reserved + r.bytes > s->opts.hbm_budget_bytes) return false;
   s->queue.pop_front();
   Slot& sl = s->slots[free_slot];
-  cudaError_t e = cudaMallocAsync(&r.ws, r.bytes, sl.st);
+  cudaStream_t rs = sl.st[r.prio];
+  cudaError_t e = cudaMallocAsync(&r.ws, r.bytes, rs);
   if (e != cudaSuccess) {
     cudaGetLastError();
     r.result = RSIM_ERR_OOM;
@@ -165,18 +174,18 @@ bool admit_one(rsim_server* s) {
   s->stats.peak_in_flight = std::max(s->stats.peak_in_flight, s->in_flight);
   void* cubes[1] = {r.r.cube};
   rsim_status st = run_frames(s->ctx, (char*)r.ws, r.bytes, r.k, &r.r.pixels, 1, cubes, r.r.tier,
-                              r.r.out_dtype, r.plan, sl.status, sl.st);
+                              r.r.out_dtype, r.plan, sl.status, rs);
   // P_valid of this request, read by retire() once the stream reaches it
   size_t o = ((sizeof(FrameIO) + 255) / 256) * 256;
-  cudaMemcpyAsync(sl.pv_host, (char*)r.ws + o, 8, cudaMemcpyDeviceToHost, sl.st);
+  cudaMemcpyAsync(sl.pv_host, (char*)r.ws + o, 8, cudaMemcpyDeviceToHost, rs);
   r.result = st;
   HostFnArg* a = new HostFnArg{s, free_slot};
-  e = cudaLaunchHostFunc(sl.st, on_complete, a);
+  e = cudaLaunchHostFunc(rs, on_complete, a);
   if (e != cudaSuccess) {
     delete a;
     cudaGetLastError();
     r.result = RSIM_ERR_CUDA;
-    cudaStreamSynchronize(sl.st);
+    cudaStreamSynchronize(rs);
     retire(s, free_slot);
     s->cv_done.notify_all();
   }
@@ -230,7 +239,13 @@ rsim_status rsim_server_create(rsim_ctx* ctx, const rsim_server_opts* opts, rsim
   for (int i = 0; i < opts->slots; ++i) {
     Slot& sl = s->slots[i];
     sl.index = i;
-    cudaError_t e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    for (int q = 0; q < kPrios && e == cudaSuccess; ++q) {
+      // greatest (numerically lowest) first, least last
+      const int pr = greatest + (least - greatest) * q / (kPrios - 1);
+      e = cudaStreamCreateWithPriority(&sl.st[q], cudaStreamNonBlocking, pr);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&sl.status, 256);
     if (e == cudaSuccess) e = cudaMemset(sl.status, 0, 256);
     if (e == cudaSuccess) e = cudaMallocHost(&sl.pv_host, 64);
@@ -261,6 +276,11 @@ rsim_status rsim_server_submit(rsim_server* s, const rsim_request* req, uint64_t
   r.plan = choose_plan(s->ctx, req->tier, r.k, req->pixels.P);
   int64_t P = req->pixels.P;
   r.bytes = batch_bytes(r.k, &P, 1, r.plan.splits, req->tier);
+  // estimated device time from the path-samples at the tier's nominal rate (CUDA cores
+  // about 6e12/s, tensor cores and the NUFFT about 6e13/s): high priority under 2 ms
+  const double work = (double)req->pixels.P * r.k.V * r.k.Ns * r.k.L;
+  const double est_ms = work / (req->tier == RSIM_TIER_FP32 ? 6e12 : 6e13) * 1e3;
+  r.prio = est_ms < 2.0 ? 0 : 1;
   std::lock_guard<std::mutex> g(s->mu);
   if (s->opts.hbm_budget_bytes && r.bytes > s->opts.hbm_budget_bytes)
     return fail(RSIM_ERR_BUDGET, "request workspace exceeds the server HBM budget");
@@ -332,6 +352,17 @@ rsim_status rsim_server_stats_get(rsim_server* s, rsim_server_stats* out) {
   return RSIM_OK;
 }
 
+rsim_status rsim_server_stats_reset(rsim_server* s) {
+  if (!s) return fail(RSIM_ERR_INVALID_ARG, "server is NULL");
+  std::lock_guard<std::mutex> g(s->mu);
+  s->stats = rsim_server_stats{};
+  s->stats.peak_reserved_bytes = s->reserved;
+  s->stats.peak_in_flight = s->in_flight;
+  s->lat_ms.clear();
+  s->have_first = false;
+  return RSIM_OK;
+}
+
 rsim_status rsim_server_destroy(rsim_server* s) {
   if (!s) return RSIM_OK;
   {
@@ -347,9 +378,10 @@ rsim_status rsim_server_destroy(rsim_server* s) {
   if (s->sched.joinable()) s->sched.join();
   cudaSetDevice(s->ctx->device);
   for (Slot& sl : s->slots) {
-    if (sl.st) {
-      cudaStreamSynchronize(sl.st);
-      cudaStreamDestroy(sl.st);
+    for (int q = 0; q < kPrios; ++q) {
+      if (!sl.st[q]) continue;
+      cudaStreamSynchronize(sl.st[q]);
+      cudaStreamDestroy(sl.st[q]);
     }
     if (sl.status) cudaFree(sl.status);
     if (sl.pv_host) cudaFreeHost(sl.pv_host);

@@ -66,6 +66,7 @@ def test_null_context_is_rejected_without_touching_a_device(lib):
     assert lib.rsim_sync_status(None, None) == _abi.ERR_INVALID_ARG
     assert lib.rsim_selftest_wait_timeout(None, 1000000, None) == _abi.ERR_INVALID_ARG
     assert lib.rsim_synth_host(None, None, None, 0, None, 0, None) == _abi.ERR_INVALID_ARG
+    assert lib.rsim_server_stats_reset(None) == _abi.ERR_INVALID_ARG
     assert lib.rsim_destroy(None) == _abi.OK
     out = ctypes.c_size_t()
     p = _abi.rsim_radar_params(2, 4, 64, 32, 3.9e-3, 0, 3e13, 1e7, 6e-5, 0, 0)

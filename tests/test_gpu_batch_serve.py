@@ -87,8 +87,18 @@ def test_server_results_equal_alone(env):
         for t in tickets:
             assert _abi.rsim_server_wait(srv, t, 60000) == _abi.OK, _abi.last_error()
         st = _abi.rsim_server_stats_get(srv)
+        # a new tally after a reset counts only the requests submitted after it
+        _abi.rsim_server_stats_reset(srv)
+        st0 = _abi.rsim_server_stats_get(srv)
+        again = [_abi.rsim_server_submit(srv, _abi.make_request(f.radar, px, _abi.TIERS[r["tier"]], cb))
+                 for r, f, px, cb in list(zip(reqs, frames, pxs, cubes))[:2]]
+        for t in again:
+            assert _abi.rsim_server_wait(srv, t, 60000) == _abi.OK, _abi.last_error()
+        st2 = _abi.rsim_server_stats_get(srv)
     finally:
         _abi.rsim_server_destroy(srv)
+    assert st0.submitted == 0 and st0.completed == 0 and st0.p50_ms == 0 and st0.busy_s == 0
+    assert st2.submitted == 2 and st2.completed == 2 and st2.p50_ms > 0
     assert st.submitted == 16 and st.completed == 16 and st.failed == 0
     assert st.p50_ms > 0 and st.p99_ms >= st.p50_ms
     assert st.peak_in_flight >= 2  # requests ran concurrently
