@@ -60,7 +60,7 @@ typedef enum {
   RSIM_ERR_TIMEOUT = 6,      /* a device-side or host-side wait ran out of time */
   RSIM_ERR_CANCELLED = 7,    /* a server request was cancelled before it ran */
   RSIM_ERR_CUDA = 8,         /* a CUDA runtime call failed (message has the detail) */
-  RSIM_ERR_UNSUPPORTED = 9,  /* valid request this build does not handle */
+  RSIM_ERR_UNSUPPORTED = 9,  /* valid request the library does not handle (shape, tier, device) */
   RSIM_ERR_NOT_FOUND = 10    /* unknown server ticket */
 } rsim_status;
 
