@@ -529,6 +529,24 @@ def run_nufft(ctx, frame, px, ref, steps, warmup):
             "unit": "T lane-op/s", "frac": round(achieved / peak, 4), "kernel_ms": round(spread_ms, 5),
             "peak_source": f"shared memory: 152 SM x 32 lanes x {clk:.0f} MHz",
             "algorithmic": "196 shared atomic lane-operations per (channel, point) record"}
+    # the accuracy each gridding kernel width buys, and its time (the same frame)
+    from dataclasses import replace as _replace
+    widths = {}
+    for w in (4, 5, 6, 7, 8):
+        rw = _replace(radar, nufft_width=w)
+        for _ in range(3):
+            ctx.synth(rw, px, "nufft", cube=cube)
+        wms = []
+        for i in range(10):
+            flush.fill_(float(i))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.synth(rw, px, "nufft", cube=cube)
+            b.record()
+            torch.cuda.synchronize()
+            wms.append(a.elapsed_time(b))
+        widths[w] = {"ms_per_step": round(statistics.median(wms), 4),
+                     "rel_err": float(oracle.rel_l2(cube.cpu().numpy(), ref))}
     t0 = time.perf_counter()
     nu.cube_nufft(radar, frame.pixels, w=7, channels=[0, 1])
     cpu_s = time.perf_counter() - t0
@@ -539,6 +557,7 @@ def run_nufft(ctx, frame, px, ref, steps, warmup):
                          "binning": prof.operand_ms / prof.calls, "spreading": spread_ms,
                          "ffts": (prof.contract_ms - prof.operand_ms) / prof.calls - spread_ms},
             "roofline": roof,
+            "by_kernel_width": widths,
             "speedup_vs_headline_tier": None,
             "cpu_baseline": {"value": pv * 2 * radar.Ns * radar.L / cpu_s / 1e9, "unit": "Gpath-samples/s",
                              "cores": 1, "kind": "oracle",

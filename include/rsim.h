@@ -72,7 +72,8 @@ typedef enum {
   RSIM_TIER_SPLIT_FP16 = 3, /* tcgen05, FP16 hi+lo operands (3 products), FP32 accumulate */
   RSIM_TIER_FP16 = 4,       /* tcgen05, FP16 operands, FP32 accumulate */
   RSIM_TIER_NUFFT = 5       /* type-1 non-uniform FFT per channel on CUDA cores: ES-kernel
-                               gridding (width 7, oversampling >= 2) with exact fixed-point
+                               gridding (width 4..8, default 7: RSIM_NUFFT_WIDTH; oversampling
+                               >= 2) with exact fixed-point
                                sums, FP32 FFTs; relative error ~1e-6.  N_s and L in 4..2048
                                (else UNSUPPORTED) */
 } rsim_tier;
@@ -103,6 +104,13 @@ typedef struct {
  * Doppler also turns the phase by -f_D m T_b across the Tx slots (a per-(pixel, channel)
  * constant added to phi).  Eq. 1 omits it (every Tx is taken at the block start). */
 #define RSIM_FLAG_TDM_MOTION 1
+
+/* NUFFT tier only: the gridding kernel's width w in cells (flags bits 8..11), which sets
+ * the accuracy: relative error about 10^-(w-1) (w = 7, the default when the bits are
+ * 0, gives ~1e-6) and a spreading cost of w^2 taps per (channel, pixel).  w in 4..8; other
+ * tiers ignore the bits. */
+#define RSIM_NUFFT_WIDTH(w) ((int32_t)(w) << 8)
+#define RSIM_NUFFT_WIDTH_MASK 0xF00
 
 /* One frame's render buffers: six arrays of P elements, flattened [el][az]
  * (structure of arrays), all of element type `dtype`.  sigma = (sigma_re, sigma_im)

@@ -178,6 +178,7 @@ def check(status: int):
 def radar_params(radar) -> rsim_radar_params:
     """Marshal a ``synth.Radar`` (or anything with the same attributes)."""
     flags = FLAG_TDM_MOTION if getattr(radar, "tdm_motion", False) else 0
+    flags |= (int(getattr(radar, "nufft_width", 0)) & 0xF) << 8
     return rsim_radar_params(int(radar.M), int(radar.N), int(radar.Ns), int(radar.L),
                              float(radar.lam), float(radar.d_rx), float(radar.mu), float(radar.fs),
                              float(radar.t_b), float(radar.t_slow), float(radar.c), flags, 0)

@@ -9,9 +9,10 @@
 // q'_p = q_p exp(j 2 pi (x_p s_x + y_p s_y)).  Each q'_p is spread onto a periodic grid of
 // G_x x G_y cells (powers of two >= 2 N_s, 2 L) with the "exponential of semicircle"
 // kernel of Barnett, Magland and af Klinteberg (SIAM J. Sci. Comput. 41, 2019),
-// psi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)), width w = 7 cells, beta = 2.30 w; the
+// psi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)), width w = 4..8 cells (7 by default),
+// beta = 2.30 w; the
 // grid's inverse-sign DFT at the centred modes, divided by the kernel's Fourier
-// transform Psi_x(n') Psi_y(l'), is the cube (relative error ~1e-6 at w = 7).
+// transform Psi_x(n') Psi_y(l'), is the cube (relative error ~10^-(w-1): ~1e-6 at w = 7).
 //
 // Kernels, per frame:
 //   nu_bin_count  each (channel, point) is binned by the 32 x 32 grid tile of its
@@ -45,11 +46,9 @@
 namespace rsim {
 namespace {
 
-constexpr int kNW = 7;                      // kernel width in cells (odd)
-constexpr int kNHalf = (kNW - 1) / 2;       // taps on each side of the nearest cell
-constexpr float kNBeta = 2.30f * kNW;       // ES shape for an oversampling of 2
+constexpr int kNWMin = 4, kNWMax = 8;       // kernel widths in cells (the default is 7)
+constexpr float kNBetaPerW = 2.30f;         // ES shape beta = 2.30 w for an oversampling of 2
 constexpr int kNTile = 32;                  // grid cells per tile side
-constexpr int kNPad = kNTile + 2 * kNHalf;  // tile side with the halo
 constexpr int kNQuad = 128;                 // midpoint nodes for Psi
 constexpr int kSpreadChunk = 256;           // records per spreading work item
 constexpr int kBinThreads = 256;            // binning blocks: one channel, kBinItems points
@@ -72,9 +71,9 @@ struct FftPlan {
 };
 
 // exp(beta (sqrt(1 - z^2) - 1)) on |z| <= 1, 0 outside
-__device__ __forceinline__ float es_kernel(float z) {
+__device__ __forceinline__ float es_kernel(float z, float beta) {
   const float z2 = z * z;
-  return z2 < 1.f ? expf(kNBeta * (sqrtf(1.f - z2) - 1.f)) : 0.f;
+  return z2 < 1.f ? expf(beta * (sqrtf(1.f - z2) - 1.f)) : 0.f;
 }
 
 // Nearest grid cell of a position (mod G, G a power of two) and the offset of the
@@ -167,11 +166,11 @@ __device__ void table_block(const NuGeo& g, const NuTables& tb, int vb) {
   float s = 0.f;
   for (int j = lane; j < kNQuad; j += 32) {
     const float z = -1.f + ((float)j + 0.5f) * (2.f / kNQuad);
-    s += es_kernel(z) * cospif((float)k * (float)kNW * z / G);
+    s += es_kernel(z, g.beta) * cospif((float)k * (float)g.W * z / G);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) {
-    const float psi = 0.5f * (float)kNW * (2.f / kNQuad) * s;
+    const float psi = 0.5f * (float)g.W * (2.f / kNQuad) * s;
     if (xs)
       inv_x[warp] = 1.f / psi;
     else
@@ -356,21 +355,43 @@ __global__ void __launch_bounds__(kBinThreads) nu_bin_fill(const FrameIO* __rest
   }
 }
 
-// Spreading layout.  A warp takes one record at a time and lane k owns tap k = kNW jx + jy
-// (lanes 0..31, then 32..48 on a second pass).  With a tile row stride of kTileStride = 7
-// (mod 32) words, the 49 taps of a record lie on consecutive banks, so each atomic
-// instruction is one shared-memory wavefront.  The weights are computed once per record
-// (one lane per record) and staged per warp: (q'_re, q'_im) psi_x by jx, psi_y by jy.
-constexpr int kTileStride = kNW + 32 * ((kNPad - kNW + 31) / 32);
-static_assert(kTileStride % 32 == kNW && kTileStride >= kNPad, "tile row stride");
-static_assert(kNW * kNW <= 64, "two passes of 32 lanes cover the taps");
-constexpr int kTileWords = (kNPad * kTileStride + 3) / 4 * 4;  // zeroed as 16-byte words
+// Spreading layout for a kernel of width W.  A warp takes one record at a time and lane k
+// owns tap k = W jx + jy (lanes 0..31, then W^2 - 32 more on a second pass for W >= 6).
+// A point's taps are the W cells whose centres lie within W/2 of it: for odd W the nearest
+// cell and (W - 1)/2 on each side, for even W the start also follows the side of the
+// nearest cell's centre the point lies on; the tile halo is H = W/2 cells.  With a tile row
+// stride of W + 32 words (W mod 32) a record's taps lie on consecutive banks, so each
+// atomic instruction is one shared-memory wavefront.  Lanes past the last tap add zero at
+// word base + lane, on banks no active lane of the pass uses.  The weights are computed
+// once per record (one lane per record) and staged per warp: (q'_re, q'_im) psi_x by jx,
+// psi_y by jy.  All of it sits in dynamic shared memory:
+//   [lo re | lo im | hi re | hi im] tile words, then the staging, then a zero row.
 constexpr int kSpreadThreads = 256;
 constexpr int kSpreadWarps = kSpreadThreads / 32;
-constexpr int kSpreadBlocksPerSm = 4;  // shared memory: 2 x 2 tile arrays + the staging
+constexpr int kSpreadBlocksPerSm = 4;  // persistent CTAs per SM (shared memory: <= 53 KB each)
 constexpr int kStageLd = 33;           // staged values of 32 records per jx (or jy), padded
 
+template <int W>
+struct SpreadLayout {
+  static constexpr int H = W / 2;                         // halo cells
+  static constexpr int PAD = kNTile + 2 * H;              // padded tile side
+  static constexpr int STRIDE = W + 32;                   // tile row stride, W (mod 32)
+  static constexpr int WORDS = (PAD * STRIDE + 3) / 4 * 4;  // one tile array, 16-byte words
+  static constexpr bool TWO = W * W > 32;                 // a second pass of lanes
+  static constexpr size_t kTiles = 4 * sizeof(unsigned) * WORDS;
+  static constexpr size_t kAx = sizeof(float2) * kSpreadWarps * W * kStageLd;
+  static constexpr size_t kWy = sizeof(float) * kSpreadWarps * W * kStageLd;
+  static constexpr size_t kBase = sizeof(int) * kSpreadWarps * 32;
+  static constexpr size_t kZero = sizeof(float2) * kStageLd;
+  static constexpr size_t bytes = kTiles + kAx + kWy + kBase + kZero;
+  static_assert(STRIDE >= PAD && STRIDE % 32 == W, "tile row stride");
+  static_assert(W * W <= 64, "two passes of 32 lanes cover the taps");
+  // a spare lane's word base + lane stays inside the tile array
+  static_assert((PAD - W) * STRIDE + (PAD - W) + 31 < WORDS, "spare-lane words in range");
+};
+
 // Persistent CTAs take the work items in turn (their number is known on the device only).
+template <int W>
 __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __restrict__ fp, NuGeo g,
                                                             const int* __restrict__ off,
                                                             const int* __restrict__ items,
@@ -379,39 +400,45 @@ __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __res
                                                             const NuRec* __restrict__ rec,
                                                             unsigned long long* __restrict__ grid,
                                                             int* __restrict__ row_used) {
+  using Lay = SpreadLayout<W>;
+  constexpr int H = Lay::H, PAD = Lay::PAD, STRIDE = Lay::STRIDE, WORDS = Lay::WORDS;
+  constexpr float beta = kNBetaPerW * W, k2w = 2.f / (float)W;
   wait_prior_grid();
-  __shared__ __align__(16) unsigned lo[2][kTileWords];  // re, im: low 16 bits of each term
-  __shared__ __align__(16) int hi[2][kTileWords];       // re, im: the signed rest
-  __shared__ float2 s_ax[kSpreadWarps][kNW][kStageLd];  // scale q' psi_x(jx)
-  __shared__ float s_wy[kSpreadWarps][kNW][kStageLd];   // psi_y(jy)
-  __shared__ int s_base[kSpreadWarps][32];              // tile word of the record's first tap
-  __shared__ float2 s_zero[kStageLd];                    // weights of the lanes idle on pass 2
+  extern __shared__ __align__(16) unsigned char smem_sp[];
+  unsigned* lo_re = reinterpret_cast<unsigned*>(smem_sp);
+  unsigned* lo_im = lo_re + WORDS;
+  int* hi_re = reinterpret_cast<int*>(lo_im + WORDS);
+  int* hi_im = hi_re + WORDS;
+  float2(*s_ax)[W][kStageLd] = reinterpret_cast<float2(*)[W][kStageLd]>(smem_sp + Lay::kTiles);
+  float(*s_wy)[W][kStageLd] = reinterpret_cast<float(*)[W][kStageLd]>(smem_sp + Lay::kTiles + Lay::kAx);
+  int(*s_base)[32] = reinterpret_cast<int(*)[32]>(smem_sp + Lay::kTiles + Lay::kAx + Lay::kWy);
+  float2* s_zero = reinterpret_cast<float2*>(smem_sp + Lay::kTiles + Lay::kAx + Lay::kWy + Lay::kBase);
   for (int i = threadIdx.x; i < kStageLd; i += blockDim.x) s_zero[i] = make_float2(0.f, 0.f);
   const int n_items = items[0];
   const int nb = g.ntx * g.nty;
   const float scale = grid_scale(*fp, false);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // This lane's taps on the two passes.  On the second pass the lanes past the last tap
-  // add zero (their x weights are the zero row) to their first-pass word, whose bank no
-  // active lane of that pass uses, so the pass needs no branch.
-  const int jx0 = lane / kNW, jy0 = lane % kNW;
-  const bool two = lane + 32 < kNW * kNW;
-  const int jx1 = two ? (lane + 32) / kNW : jx0, jy1 = two ? (lane + 32) % kNW : jy0;
-  const int off0 = jx0 * kTileStride + jy0, off1 = jx1 * kTileStride + jy1;
-  const float2* ax0 = s_ax[warp][jx0];
-  const float2* ax1 = two ? s_ax[warp][jx1] : s_zero;
+  // This lane's taps on the two passes (a spare lane: the zero row, word base + lane).
+  const bool act0 = lane < W * W;
+  const int jx0 = act0 ? lane / W : 0, jy0 = act0 ? lane % W : 0;
+  const int off0 = act0 ? jx0 * STRIDE + jy0 : lane;
+  const bool act1 = lane + 32 < W * W;
+  const int jx1 = act1 ? (lane + 32) / W : 0, jy1 = act1 ? (lane + 32) % W : 0;
+  const int off1 = act1 ? jx1 * STRIDE + jy1 : off0;
+  const float2* ax0 = act0 ? s_ax[warp][jx0] : s_zero;
+  const float2* ax1 = act1 ? s_ax[warp][jx1] : s_zero;
   const float* wy0 = s_wy[warp][jy0];
   const float* wy1 = s_wy[warp][jy1];
   const int* sb = s_base[warp];
   auto pass = [&](int base, float2 a, float w, int offs) {
     const int at = base + offs;
-    add_split(&lo[0][at], &hi[0][at], __float2int_rn(a.x * w));
-    add_split(&lo[1][at], &hi[1][at], __float2int_rn(a.y * w));
+    add_split(&lo_re[at], &hi_re[at], __float2int_rn(a.x * w));
+    add_split(&lo_im[at], &hi_im[at], __float2int_rn(a.y * w));
   };
   auto taps = [&](int r) {
     const int base = sb[r];
     pass(base, ax0[r], wy0[r], off0);
-    pass(base, ax1[r], wy1[r], off1);
+    if (Lay::TWO) pass(base, ax1[r], wy1[r], off1);
   };
   for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
     const int bin = item_bin[item];
@@ -420,15 +447,10 @@ __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __res
     const int r_end = min(off[bin + 1], r_begin + kSpreadChunk);
     // the grid rows this item adds to (the padded tile's, mod G_x): the row pass skips
     // rows that no item marks, which hold zeros only
-    for (int r = threadIdx.x; r < kNPad; r += blockDim.x)
-      row_used[(int64_t)v * g.Gx + ((tx * g.Tx - kNHalf + r) & (g.Gx - 1))] = 1;
-    for (int i = threadIdx.x; i < kTileWords / 4; i += blockDim.x) {
-      const uint4 z = make_uint4(0u, 0u, 0u, 0u);
-      reinterpret_cast<uint4*>(lo[0])[i] = z;
-      reinterpret_cast<uint4*>(lo[1])[i] = z;
-      reinterpret_cast<uint4*>(hi[0])[i] = z;
-      reinterpret_cast<uint4*>(hi[1])[i] = z;
-    }
+    for (int r = threadIdx.x; r < PAD; r += blockDim.x)
+      row_used[(int64_t)v * g.Gx + ((tx * g.Tx - H + r) & (g.Gx - 1))] = 1;
+    for (int i = threadIdx.x; i < WORDS; i += blockDim.x)  // 4 arrays of WORDS / 4 16-byte words
+      reinterpret_cast<uint4*>(smem_sp)[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     for (int r0 = r_begin + warp * 32; r0 < r_end; r0 += kSpreadThreads) {
       const int n = min(32, r_end - r0);
@@ -438,17 +460,19 @@ __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __res
         float dx, dy;
         nearest_cell(q.x, g.Gx, cx, dx);
         nearest_cell(q.y, g.Gy, cy, dy);
+        // first tap relative to the nearest cell
+        const int sx = (W & 1) ? -(W - 1) / 2 : -W / 2 + (dx >= 0.f ? 1 : 0);
+        const int sy = (W & 1) ? -(W - 1) / 2 : -W / 2 + (dy >= 0.f ? 1 : 0);
         // the nearest cell lies in this tile: local padded coordinates of the first tap
-        const int lx = cx - tx * g.Tx, ly = cy - ty * g.Ty;
+        const int lx = cx - tx * g.Tx + H + sx, ly = cy - ty * g.Ty + H + sy;
         const float qr = q.q.x * scale, qi = q.q.y * scale;
 #pragma unroll
-        for (int j = 0; j < kNW; ++j) {
-          constexpr float k2w = 2.f / (float)kNW;
-          const float wx = es_kernel(((float)(j - kNHalf) - dx) * k2w);
+        for (int j = 0; j < W; ++j) {
+          const float wx = es_kernel(((float)(sx + j) - dx) * k2w, beta);
           s_ax[warp][j][lane] = make_float2(qr * wx, qi * wx);
-          s_wy[warp][j][lane] = es_kernel(((float)(j - kNHalf) - dy) * k2w);
+          s_wy[warp][j][lane] = es_kernel(((float)(sy + j) - dy) * k2w, beta);
         }
-        s_base[warp][lane] = lx * kTileStride + ly;
+        s_base[warp][lane] = lx * STRIDE + ly;
       }
       __syncwarp();
       int r = 0;
@@ -460,12 +484,12 @@ __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __res
       __syncwarp();
     }
     __syncthreads();
-    const int x0 = tx * g.Tx - kNHalf, y0 = ty * g.Ty - kNHalf;  // padded tile origin (cells)
+    const int x0 = tx * g.Tx - H, y0 = ty * g.Ty - H;  // padded tile origin (cells)
     const int64_t gbase = (int64_t)v * g.Gx * g.Gy;
-    for (int i = threadIdx.x; i < kNPad * kNPad; i += blockDim.x) {
-      const int row = i / kNPad, col = i % kNPad, at = row * kTileStride + col;
-      const long long re = ((long long)hi[0][at] << 16) + (long long)lo[0][at];
-      const long long im = ((long long)hi[1][at] << 16) + (long long)lo[1][at];
+    for (int i = threadIdx.x; i < PAD * PAD; i += blockDim.x) {
+      const int row = i / PAD, col = i % PAD, at = row * STRIDE + col;
+      const long long re = ((long long)hi_re[at] << 16) + (long long)lo_re[at];
+      const long long im = ((long long)hi_im[at] << 16) + (long long)lo_im[at];
       if (re == 0 && im == 0) continue;
       const int gx = (x0 + row) & (g.Gx - 1), gy = (y0 + col) & (g.Gy - 1);
       unsigned long long* cell = grid + 2 * (gbase + (int64_t)gx * g.Gy + gy);
@@ -843,12 +867,16 @@ NuGeo nufft_geometry(const Consts& k, int64_t P) {
   g.sx = k.Ns / 2;
   g.sy = k.L / 2;
   g.P = std::max<int64_t>(P, 1);
+  g.W = k.nu_w;
+  g.beta = kNBetaPerW * (float)g.W;
   return g;
 }
 
 bool nufft_supported(const Consts& k) {
-  // FFT lengths up to 4096 in one CTA's shared memory, at least 8 cells per axis
-  return 2 * (int64_t)k.Ns <= 4096 && 2 * (int64_t)k.L <= 4096 && k.Ns >= 4 && k.L >= 4;
+  // FFT lengths up to 4096 in one CTA's shared memory, at least 8 cells per axis, and a
+  // kernel width with a spreading kernel
+  return 2 * (int64_t)k.Ns <= 4096 && 2 * (int64_t)k.L <= 4096 && k.Ns >= 4 && k.L >= 4 && k.nu_w >= kNWMin &&
+         k.nu_w <= kNWMax;
 }
 
 size_t nufft_scratch_bytes(const Consts& k, int64_t P) {
@@ -889,10 +917,23 @@ cudaError_t launch_nufft(const Consts& k, const FrameIO* frame, int64_t P, int o
                        sc.count, tb, it);
   if (e == cudaSuccess)
     e = launch_dependent(nu_bin_fill, bgrid, dim3(kBinThreads), (size_t)(8 * nb), st, frame, g, sc.cursor, sc.rec);
+  // the spreading kernel of the gridding kernel's width, and its shared memory
+  using SpreadFn = void (*)(const FrameIO*, NuGeo, const int*, const int*, const int*, const int*, const NuRec*,
+                            unsigned long long*, int*);
+  SpreadFn spread = nu_spread<7>;
+  size_t spread_smem = SpreadLayout<7>::bytes;
+  switch (g.W) {
+    case 4: spread = nu_spread<4>; spread_smem = SpreadLayout<4>::bytes; break;
+    case 5: spread = nu_spread<5>; spread_smem = SpreadLayout<5>::bytes; break;
+    case 6: spread = nu_spread<6>; spread_smem = SpreadLayout<6>::bytes; break;
+    case 8: spread = nu_spread<8>; spread_smem = SpreadLayout<8>::bytes; break;
+    default: break;
+  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(spread, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spread_smem);
   if (e == cudaSuccess && spread_begin) e = cudaEventRecord(spread_begin, st);
   if (e == cudaSuccess)
-    e = launch_dependent(nu_spread, dim3((unsigned)std::min<int64_t>(max_items, kSpreadBlocksPerSm * num_sms)),
-                         dim3(kSpreadThreads), 0, st, frame, g, (const int*)sc.off,
+    e = launch_dependent(spread, dim3((unsigned)std::min<int64_t>(max_items, kSpreadBlocksPerSm * num_sms)),
+                         dim3(kSpreadThreads), spread_smem, st, frame, g, (const int*)sc.off,
                          (const int*)sc.items, (const int*)sc.item_bin, (const int*)sc.item_first,
                          (const NuRec*)sc.rec, sc.grid, sc.row_used);
   if (e == cudaSuccess && spread_end) e = cudaEventRecord(spread_end, st);

@@ -95,8 +95,12 @@ rsim_status check_params(const rsim_radar_params* p, Consts* k) {
   k->k_da = p->mu * d / (c * p->fs);
   k->k_g = d / p->lambda;
   k->k_b = -2.0 * ts / p->lambda;
-  if (p->flags & ~RSIM_FLAG_TDM_MOTION) return fail(RSIM_ERR_INVALID_ARG, "unknown flag bits");
+  if (p->flags & ~(RSIM_FLAG_TDM_MOTION | RSIM_NUFFT_WIDTH_MASK))
+    return fail(RSIM_ERR_INVALID_ARG, "unknown flag bits");
   k->k_m = (p->flags & RSIM_FLAG_TDM_MOTION) ? -2.0 * p->t_b / p->lambda : 0.0;
+  const int w = (p->flags & RSIM_NUFFT_WIDTH_MASK) >> 8;
+  if (w != 0 && (w < 4 || w > 8)) return fail(RSIM_ERR_INVALID_ARG, "the NUFFT kernel width must be 4..8");
+  k->nu_w = w ? w : 7;
   return RSIM_OK;
 }
 

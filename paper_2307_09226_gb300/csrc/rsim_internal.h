@@ -25,6 +25,7 @@ constexpr int kMaxSplits = 64;
 struct Consts {
   int M, N, V, Ns, L;
   double k_a0, k_da, k_g, k_b, k_m;
+  int nu_w;  // NUFFT tier: gridding kernel width (cells)
 };
 
 // One frame as the kernels see it: caller buffers plus this frame's workspace slices.
@@ -85,6 +86,8 @@ struct NuGeo {
   int ntx, nty;   // tiles per axis
   int sx, sy;     // centring shifts Ns / 2, L / 2
   int64_t P;      // pixel bound (items per channel)
+  int W;          // gridding kernel width (cells)
+  float beta;     // its shape parameter, 2.30 W
 };
 // Kernels launch_nufft starts per frame (binning with the tables and the scan, record
 // fill, spreading, two FFT passes).

@@ -44,6 +44,7 @@ class Radar:
     t_slow: float = 0.0  # TDM block period [s]; <= 0 means M * t_b
     c: float = C_LIGHT
     tdm_motion: bool = False  # add the Doppler phase of the Tx slot within a block
+    nufft_width: int = 0  # NUFFT tier: gridding kernel width 4..8 (0: the default, 7)
 
     @property
     def V(self) -> int:

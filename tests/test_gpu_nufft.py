@@ -31,6 +31,28 @@ def test_gpu_matches_cpu_nufft_at_width_7(ctx):
     assert e_gpu <= 2e-5
 
 
+def test_kernel_widths(ctx):
+    # every width against the CPU NUFFT at that width (implementation error only), and
+    # against the exact sum: the error falls by orders of magnitude as the width grows
+    from dataclasses import replace
+    f = synth.parity_frame(seed=52, M=2, N=2, Ns=64, L=32, n_az=40, n_el=30)
+    ref = oracle.cube_separable(f.radar, f.pixels)
+    errs = {}
+    for w in (4, 5, 6, 7, 8):
+        radar = replace(f.radar, nufft_width=w)
+        got = ctx.synth(radar, device.upload(f), "nufft").cpu().numpy()
+        cpu = nu.cube_nufft(radar, f.pixels, w=w)
+        assert oracle.rel_l2(got, cpu) <= 5e-6, w
+        errs[w] = oracle.rel_l2(got, ref)
+    print("gpu nufft vs exact by width", {w: f"{e:.1e}" for w, e in errs.items()})
+    assert all(errs[w + 1] < 0.3 * errs[w] for w in (4, 5, 6))
+    assert errs[7] <= 5e-6 and errs[4] > 1e-4
+    for bad in (3, 9):
+        with pytest.raises(_abi.RsimError) as e:
+            ctx.synth(replace(f.radar, nufft_width=bad), device.upload(f), "nufft")
+        assert e.value.status == _abi.ERR_INVALID_ARG
+
+
 def test_crowded_grid_cell(ctx):
     # every pixel at nearly the same range and speed: all points land in one grid tile,
     # which the work items share among many CTAs
