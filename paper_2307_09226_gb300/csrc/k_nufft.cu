@@ -7,12 +7,12 @@
 //
 // Centred modes n = n' + s_x, l = l' + s_y move the shift into the strengths,
 // q'_p = q_p exp(j 2 pi (x_p s_x + y_p s_y)).  Each q'_p is spread onto a periodic grid of
-// G_x x G_y cells (powers of two >= 2 N_s, 2 L) with the "exponential of semicircle"
-// kernel of Barnett, Magland and af Klinteberg (SIAM J. Sci. Comput. 41, 2019),
-// psi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)), width w = 4..8 cells (7 by default),
-// beta = 2.30 w; the
-// grid's inverse-sign DFT at the centred modes, divided by the kernel's Fourier
-// transform Psi_x(n') Psi_y(l'), is the cube (relative error ~10^-(w-1): ~1e-6 at w = 7).
+// G_x x G_y cells (powers of two >= 2 N_s, 2 L, and >= 16) with the "exponential of
+// semicircle" kernel of Barnett, Magland and af Klinteberg (SIAM J. Sci. Comput. 41,
+// 2019), psi(t) = exp(beta (sqrt(1 - (2t/w)^2) - 1)), width w = 4..8 cells (7 by default),
+// beta = 2.30 w; the grid's inverse-sign DFT at the centred modes, divided by the kernel's
+// Fourier transform Psi_x(n') Psi_y(l'), is the cube (relative error ~10^-(w-1): ~1e-6
+// at w = 7).
 //
 // Kernels, per frame:
 //   nu_bin_count  each (channel, point) is binned by the 32 x 32 grid tile of its
@@ -26,7 +26,7 @@
 //                 (block, bin), ranks within the block from shared memory);
 //   nu_spread     persistent CTAs take the work items in turn; a warp takes one record
 //                 at a time, lane k adding tap k of its w x w taps into a shared-memory tile
-//                 with a (w - 1) / 2 halo, as fixed-point integers (each term split in
+//                 with a w/2 halo, as fixed-point integers (each term split in
 //                 16-bit halves summed by non-returning 32-bit atomics), then the tile is
 //                 added into the global 64-bit integer grid.  Integer sums are exact and do
 //                 not depend on the order of the atomic additions, so the result is
