@@ -162,11 +162,15 @@ rsim_status rsim_synth(rsim_ctx* ctx, const rsim_radar_params* params, const rsi
  * ([M*N][Ns][L] complex64 or complex128) are HOST pointers.  The call copies the pixel
  * arrays into a device staging buffer owned by the context (one cudaMemcpyAsync per
  * array), synthesises the cube there exactly as rsim_synth does, and copies it back
- * (one cudaMemcpyAsync), all on `stream`.  The host buffers must stay valid and
- * unchanged until the stream has passed the copies (e.g. rsim_sync_status); with
- * page-locked host memory the copies are asynchronous, with pageable memory they block
- * the calling thread.  The staging buffer grows when needed (cudaMalloc after one
- * stream synchronisation) and counts against the context's budget with the workspace.
+ * (one cudaMemcpyAsync), all on `stream`.  When the pixel arrays are reachable from the
+ * device (page-locked memory, or any host memory on a node whose GPU reads pageable
+ * memory through the host page tables, as over NVLink-C2C), the kernels read them in
+ * place instead of copies; the cube is always staged and copied back in one piece.
+ * Either way the results are those of rsim_synth, and the host buffers must stay valid
+ * and unchanged until the stream has passed the call's work (e.g. rsim_sync_status); with
+ * pageable memory and no direct access the copies block the calling thread.  The staging buffer grows when
+ * needed (cudaMalloc after one stream synchronisation) and counts against the context's
+ * budget with the workspace.
  * Errors: as rsim_synth. */
 rsim_status rsim_synth_host(rsim_ctx* ctx, const rsim_radar_params* params, const rsim_pixels* pixels,
                             rsim_tier tier, void* cube, int32_t out_dtype, rsim_stream stream);

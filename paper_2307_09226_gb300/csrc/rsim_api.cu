@@ -394,6 +394,30 @@ rsim_status rsim_synth(rsim_ctx* ctx, const rsim_radar_params* params, const rsi
   return rsim_synth_batch(ctx, params, pixels, 1, cubes, tier, out_dtype, stream);
 }
 
+// A pointer the device can use for host buffer `p`, or nullptr: page-locked (registered)
+// memory through its mapped address, device or managed memory as is, and pageable memory
+// only when the device reads it through the host's page tables.
+const void* device_view(rsim_ctx* ctx, const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+  if (ctx->pageable_access < 0) {
+    int pma = 0, tables = 0;
+    if (cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, ctx->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&tables, cudaDevAttrPageableMemoryAccessUsesHostPageTables, ctx->device) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      pma = tables = 0;
+    }
+    ctx->pageable_access = (pma && tables) ? 1 : 0;
+  }
+  return ctx->pageable_access == 1 ? p : nullptr;
+}
+
 rsim_status rsim_synth_host(rsim_ctx* ctx, const rsim_radar_params* params, const rsim_pixels* pixels,
                             rsim_tier tier, void* cube, int32_t out_dtype, rsim_stream stream) {
   if (!ctx) return fail(RSIM_ERR_INVALID_ARG, "ctx is NULL");
@@ -408,10 +432,19 @@ rsim_status rsim_synth_host(rsim_ctx* ctx, const rsim_radar_params* params, cons
   const size_t elem = pixels->dtype == RSIM_F64 ? 8 : 4;
   const size_t arr = align_up((size_t)pixels->P * elem, 256);
   const size_t cube_bytes = (size_t)k.V * (size_t)k.Ns * (size_t)k.L * (out_dtype == RSIM_C128 ? 16 : 8);
-  const size_t need = 6 * arr + cube_bytes;
+  const size_t cube_span = align_up(cube_bytes, 256);
+  size_t need = cube_span + 6 * arr;
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
+  // pixel arrays the device can read in place (coalesced loads over the host link) are not
+  // staged; the cube always is, and comes back in one copy (the kernels that write it
+  // scatter 8- to 16-byte stores, which cross the host link one by one)
+  const void* src[6] = {pixels->range, pixels->sigma_re, pixels->sigma_im, pixels->az, pixels->el, pixels->vel};
+  const void* view[6] = {};
+  bool direct = pixels->P > 0;
+  for (int i = 0; i < 6 && direct; ++i) direct = (view[i] = device_view(ctx, src[i])) != nullptr;
+  if (direct) need = cube_bytes;
   if (ctx->stage_bytes < need) {
     if (ctx->budget && ctx->ws_bytes + need > ctx->budget)
       return fail(RSIM_ERR_BUDGET, "staging of " + std::to_string(need) + " bytes exceeds the context budget");
@@ -428,17 +461,20 @@ rsim_status rsim_synth_host(rsim_ctx* ctx, const rsim_radar_params* params, cons
     ctx->stage_bytes = need;
   }
   char* base = (char*)ctx->stage;
-  const void* src[6] = {pixels->range, pixels->sigma_re, pixels->sigma_im, pixels->az, pixels->el, pixels->vel};
   rsim_pixels dev = *pixels;
   const void** dst[6] = {&dev.range, &dev.sigma_re, &dev.sigma_im, &dev.az, &dev.el, &dev.vel};
   for (int i = 0; i < 6; ++i) {
-    *dst[i] = base + i * arr;
+    if (direct) {
+      *dst[i] = view[i];
+      continue;
+    }
+    *dst[i] = base + cube_span + i * arr;
     if (pixels->P > 0) {
-      e = cudaMemcpyAsync(base + i * arr, src[i], (size_t)pixels->P * elem, cudaMemcpyHostToDevice, st);
+      e = cudaMemcpyAsync(base + cube_span + i * arr, src[i], (size_t)pixels->P * elem, cudaMemcpyHostToDevice, st);
       if (e != cudaSuccess) return cuda_fail(e, "copy of a pixel array to the device");
     }
   }
-  void* cube_dev = base + 6 * arr;
+  void* cube_dev = base;
   s = rsim_synth(ctx, params, &dev, tier, cube_dev, out_dtype, stream);
   if (s != RSIM_OK) return s;
   e = cudaMemcpyAsync(cube, cube_dev, cube_bytes, cudaMemcpyDeviceToHost, st);

@@ -22,6 +22,7 @@ struct rsim_ctx {
   unsigned* status_dev = nullptr;
   void* stage = nullptr;  // rsim_synth_host: device copies of the pixel arrays and the cube
   size_t stage_bytes = 0;
+  int pageable_access = -1;  // the device reads pageable host memory through the host page tables (-1: not asked yet)
   std::mutex plan_mu;
   std::map<std::string, rsim_plan> plans;
   // stage profiling (rsim_profile_enable / rsim_profile_read)
