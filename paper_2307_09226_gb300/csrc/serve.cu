@@ -83,7 +83,13 @@ struct rsim_server {
   bool have_first = false;
   rsim::Clock::time_point t_first, t_last;
   int in_flight = 0;
-  std::vector<int> completed_slots;  // slots whose host function fired, to be retired
+  // Slots whose host function fired, to be retired.  Guarded by cb_mu alone, which is
+  // never held across a CUDA call: the host function runs on CUDA's callback thread, and
+  // a CUDA call made while holding a lock it needs (the scheduler launches work holding
+  // `mu`; a launch that first loads a kernel module can wait for device work, including
+  // that host function) would never return.
+  std::mutex cb_mu;
+  std::vector<int> completed_slots;
 };
 
 namespace rsim {
@@ -99,10 +105,10 @@ void CUDART_CB on_complete(void* p) {
   HostFnArg* a = (HostFnArg*)p;
   rsim_server* s = a->s;
   {
-    std::lock_guard<std::mutex> g(s->mu);
+    std::lock_guard<std::mutex> g(s->cb_mu);
     s->completed_slots.push_back(a->slot);
   }
-  s->cv_sched.notify_all();
+  s->cv_sched.notify_all();  // a missed wake-up costs at most the scheduler's 50 ms poll
   delete a;
 }
 
@@ -197,16 +203,22 @@ void scheduler(rsim_server* s) {
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     bool progressed = false;
-    while (!s->completed_slots.empty()) {
-      int si = s->completed_slots.back();
-      s->completed_slots.pop_back();
+    std::vector<int> done;
+    {
+      std::lock_guard<std::mutex> g(s->cb_mu);
+      done.swap(s->completed_slots);
+    }
+    for (int si : done) {
       retire(s, si);
       progressed = true;
     }
     if (progressed) s->cv_done.notify_all();
     while (!s->stop && admit_one(s)) {
     }
-    if (s->stop && s->in_flight == 0 && s->completed_slots.empty()) break;
+    if (s->stop && s->in_flight == 0) {
+      std::lock_guard<std::mutex> g(s->cb_mu);
+      if (s->completed_slots.empty()) break;
+    }
     s->cv_sched.wait_for(lk, std::chrono::milliseconds(50));
   }
 }

@@ -20,7 +20,7 @@ from paper_2307_09226_gb300.synth import Radar
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 2e-5, "split_fp16": 2e-5, "split_bf16": 2e-5, "bf16": 1e-2, "fp16": 1e-2}
+TOL = {"fp32": 2e-5, "split_fp16": 2e-5, "split_bf16": 2e-5, "bf16": 1e-2, "fp16": 1e-2, "nufft": 2e-5}
 
 
 @pytest.fixture(scope="module")
@@ -69,7 +69,8 @@ def test_batch_with_uneven_pixel_counts(env):
 
 
 def _requests(n, seed=5):
-    reqs = synth.serving_requests(n, seed=seed, grids=(32, 48, 64), tiers=("fp32", "split_bf16", "split_fp16"))
+    reqs = synth.serving_requests(n, seed=seed, grids=(32, 48, 64),
+                                  tiers=("fp32", "split_bf16", "split_fp16", "nufft"))
     return reqs
 
 
