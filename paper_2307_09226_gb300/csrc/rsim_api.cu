@@ -470,14 +470,16 @@ rsim_status rsim_synth_host(rsim_ctx* ctx, const rsim_radar_params* params, cons
     }
     *dst[i] = base + cube_span + i * arr;
     if (pixels->P > 0) {
-      e = cudaMemcpyAsync(base + cube_span + i * arr, src[i], (size_t)pixels->P * elem, cudaMemcpyHostToDevice, st);
+      // cudaMemcpyDefault: the direction follows the pointers (unified addressing), so a
+      // caller may also pass device or managed memory here
+      e = cudaMemcpyAsync(base + cube_span + i * arr, src[i], (size_t)pixels->P * elem, cudaMemcpyDefault, st);
       if (e != cudaSuccess) return cuda_fail(e, "copy of a pixel array to the device");
     }
   }
   void* cube_dev = base;
   s = rsim_synth(ctx, params, &dev, tier, cube_dev, out_dtype, stream);
   if (s != RSIM_OK) return s;
-  e = cudaMemcpyAsync(cube, cube_dev, cube_bytes, cudaMemcpyDeviceToHost, st);
+  e = cudaMemcpyAsync(cube, cube_dev, cube_bytes, cudaMemcpyDefault, st);
   if (e != cudaSuccess) return cuda_fail(e, "copy of the cube to the host");
   return RSIM_OK;
 }
