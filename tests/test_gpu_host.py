@@ -52,3 +52,18 @@ def test_device_tensors_are_rejected(ctx):
     f = synth.parity_frame(seed=3, n_az=8, n_el=8)
     with pytest.raises(ValueError):
         ctx.synth_host(f.radar, device.upload(f), "fp32")
+
+
+@pytest.mark.parametrize("tier,out_dtype", [("fp32", "complex64"), ("split_fp16", "complex64"),
+                                            ("split_bf16", "complex128")])
+def test_host_call_row_ranges(ctx, tier, out_dtype):
+    """A full-size frame whose pixels are split across several partial sums: the host
+    call's cube equals the device call's bit for bit."""
+    f = synth.config2()
+    want = ctx.synth(f.radar, device.upload(f), tier, out_dtype=out_dtype).cpu().numpy()
+    plan = _abi.rsim_get_plan(ctx.h, f.radar, f.pixels.P, _abi.TIERS[tier])
+    assert plan.splits > 1  # the split reduction runs
+    got = ctx.synth_host(f.radar, _host(f, True), tier, out_dtype=out_dtype)
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == _abi.OK
+    assert np.array_equal(got.numpy(), want)
