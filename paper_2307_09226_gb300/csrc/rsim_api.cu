@@ -156,14 +156,17 @@ size_t frames_bytes(const Consts& k, const int64_t* P, int F, int splits, int ti
   return o;
 }
 
-// Workspace bytes for F frames: the per-frame regions, then (NUFFT tier) one grid
-// scratch that the frames use in turn.
+// Grid scratch slots of a NUFFT batch: one per stream its frames run on.
+int nufft_slots(int F) { return std::max(1, std::min(F, rsim_ctx::kNuStreams)); }
+
+// Workspace bytes for F frames: the per-frame regions, then (NUFFT tier) the grid
+// scratch slots that the frames use in turn.
 size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits, int tier) {
   size_t o = frames_bytes(k, P, F, splits, tier);
   if (tier == RSIM_TIER_NUFFT) {
     int64_t mp = 0;
     for (int f = 0; f < F; ++f) mp = std::max(mp, P[f]);
-    o = align_up(o, 256) + nufft_scratch_bytes(k, mp);
+    o = align_up(o, 256) + (size_t)nufft_slots(F) * align_up(nufft_scratch_bytes(k, mp), 256);
   }
   return o;
 }
@@ -290,11 +293,40 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   if (tier == RSIM_TIER_NUFFT) {
     if (!nufft_supported(k)) return fail(RSIM_ERR_UNSUPPORTED, "the NUFFT tier needs N_s and L in 4..2048");
     char* scratch = ws + align_up(frames_bytes(k, Ps.data(), F, splits, tier), 256);
+    const size_t slot = align_up(nufft_scratch_bytes(k, mp), 256);
+    const int S = nufft_slots(F);
+    if (S > 1 && !ctx->nu_st[0]) {
+      for (int i = 0; i < rsim_ctx::kNuStreams; ++i) {
+        e = cudaStreamCreateWithFlags(&ctx->nu_st[i], cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+          ctx->nu_st[i] = nullptr;
+          return cuda_fail(e, "cudaStreamCreate (NUFFT streams)");
+        }
+      }
+      for (cudaEvent_t& x : ctx->nu_ev) {
+        e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate (NUFFT streams)");
+      }
+    }
+    // frame f runs on stream f mod S with scratch slot f mod S; every stream first waits
+    // for the compaction and phases on `st`, and `st` then waits for every stream
+    if (S > 1) {
+      e = cudaEventRecord(ctx->nu_ev[rsim_ctx::kNuStreams], st);
+      for (int i = 0; i < S && e == cudaSuccess; ++i)
+        e = cudaStreamWaitEvent(ctx->nu_st[i], ctx->nu_ev[rsim_ctx::kNuStreams], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "fork of the NUFFT streams");
+    }
     for (int f = 0; f < F; ++f) {
       // the first frame's spreading kernel is bracketed by ev[4] and ev[5]
-      e = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch, status, st, prof && f == 0 ? ev[4] : nullptr,
-                       prof && f == 0 ? ev[5] : nullptr);
+      cudaStream_t fs = S > 1 ? ctx->nu_st[f % S] : st;
+      e = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch + (size_t)(f % S) * slot, status, fs,
+                       prof && f == 0 ? ev[4] : nullptr, prof && f == 0 ? ev[5] : nullptr);
       if (e != cudaSuccess) return cuda_fail(e, "NUFFT kernels");
+    }
+    for (int i = 0; i < S && S > 1; ++i) {
+      e = cudaEventRecord(ctx->nu_ev[i], ctx->nu_st[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->nu_ev[i], 0);
+      if (e != cudaSuccess) return cuda_fail(e, "join of the NUFFT streams");
     }
     if (prof) cudaEventRecord(ev[2], st);
   } else if (tier == RSIM_TIER_FP32) {
@@ -371,6 +403,10 @@ rsim_status rsim_destroy(rsim_ctx* ctx) {
   if (ctx->stage) cudaFree(ctx->stage);
   if (ctx->status_dev) cudaFree(ctx->status_dev);
   for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->nu_ev)
+    if (e) cudaEventDestroy(e);
+  for (cudaStream_t s : ctx->nu_st)
+    if (s) cudaStreamDestroy(s);
   delete ctx;
   return RSIM_OK;
 }

@@ -23,6 +23,11 @@ struct rsim_ctx {
   void* stage = nullptr;  // rsim_synth_host: device copies of the pixel arrays and the cube
   size_t stage_bytes = 0;
   int pageable_access = -1;  // the device reads pageable host memory through the host page tables (-1: not asked yet)
+  // NUFFT batches: frames run on kNuStreams streams, each with its own grid scratch, so
+  // that the kernels of small frames overlap (created on first use)
+  static constexpr int kNuStreams = 4;
+  cudaStream_t nu_st[kNuStreams] = {};
+  cudaEvent_t nu_ev[kNuStreams + 1] = {};  // one per stream, then the fork
   std::mutex plan_mu;
   std::map<std::string, rsim_plan> plans;
   // stage profiling (rsim_profile_enable / rsim_profile_read)
