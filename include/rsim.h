@@ -181,7 +181,7 @@ rsim_status rsim_synth_host(rsim_ctx* ctx, const rsim_radar_params* params, cons
  * counter, longest first.  frames: HOST array of F descriptors; cubes: HOST array
  * of F device pointers, each laid out as in rsim_synth.  Each frame's result is
  * bit-identical to rsim_synth of that frame alone with the same tier.  The NUFFT tier
- * runs the frames on up to four streams of the context (each with its own grid
+ * runs the frames on up to eight streams of the context (each with its own grid
  * scratch), which wait for `stream` first; `stream` then waits for all of them, so the
  * call stays ordered on `stream` like every other.
  * Errors: as rsim_synth. */

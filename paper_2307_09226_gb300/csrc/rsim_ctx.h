@@ -25,7 +25,7 @@ struct rsim_ctx {
   int pageable_access = -1;  // the device reads pageable host memory through the host page tables (-1: not asked yet)
   // NUFFT batches: frames run on kNuStreams streams, each with its own grid scratch, so
   // that the kernels of small frames overlap (created on first use)
-  static constexpr int kNuStreams = 4;
+  static constexpr int kNuStreams = 8;
   cudaStream_t nu_st[kNuStreams] = {};
   cudaEvent_t nu_ev[kNuStreams + 1] = {};  // one per stream, then the fork
   std::mutex plan_mu;
