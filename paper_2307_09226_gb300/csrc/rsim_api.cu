@@ -316,18 +316,20 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
         e = cudaStreamWaitEvent(ctx->nu_st[i], ctx->nu_ev[rsim_ctx::kNuStreams], 0);
       if (e != cudaSuccess) return cuda_fail(e, "fork of the NUFFT streams");
     }
-    for (int f = 0; f < F; ++f) {
+    cudaError_t le = cudaSuccess;
+    for (int f = 0; f < F && le == cudaSuccess; ++f) {
       // the first frame's spreading kernel is bracketed by ev[4] and ev[5]
       cudaStream_t fs = S > 1 ? ctx->nu_st[f % S] : st;
-      e = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch + (size_t)(f % S) * slot, status, fs,
-                       prof && f == 0 ? ev[4] : nullptr, prof && f == 0 ? ev[5] : nullptr);
-      if (e != cudaSuccess) return cuda_fail(e, "NUFFT kernels");
+      le = launch_nufft(k, table + f, frames[f].P, out_dtype, scratch + (size_t)(f % S) * slot, status, fs,
+                        prof && f == 0 ? ev[4] : nullptr, prof && f == 0 ? ev[5] : nullptr);
     }
+    // the join also follows a failed launch, so that nothing of this call runs on after it
     for (int i = 0; i < S && S > 1; ++i) {
       e = cudaEventRecord(ctx->nu_ev[i], ctx->nu_st[i]);
       if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ctx->nu_ev[i], 0);
       if (e != cudaSuccess) return cuda_fail(e, "join of the NUFFT streams");
     }
+    if (le != cudaSuccess) return cuda_fail(le, "NUFFT kernels");
     if (prof) cudaEventRecord(ev[2], st);
   } else if (tier == RSIM_TIER_FP32) {
     if (prof) cudaEventRecord(ev[4], st);
