@@ -74,6 +74,26 @@ def test_batch_equals_alone_bitwise(ctx):
         assert np.array_equal(a, b) and np.array_equal(a, c)
 
 
+def test_batch_reusing_streams_and_scratch_bitwise(ctx):
+    """More frames than the library's NUFFT streams (eight): later frames reuse a
+    stream and its grid scratch after an earlier frame; every frame, including the
+    empty one, still equals its single-frame result bit for bit."""
+    frames = synth.walking_batch(n_frames=11, n_az=64, n_el=48)
+    radar = frames[0].radar
+    px0 = frames[3].pixels
+    px0.sigma_re[:] = 0.0
+    px0.sigma_im[:] = 0.0
+    frames[3] = synth.Frame(radar, px0, frames[3].out_dtype)
+    pxs = [device.upload(f) for f in frames]
+    alone = [ctx.synth(radar, px, "nufft").cpu().numpy() for px in pxs]
+    batch = [c.cpu().numpy() for c in ctx.synth_batch(radar, pxs, "nufft")]
+    torch.cuda.synchronize()
+    assert ctx.sync_status() == _abi.OK
+    assert np.all(alone[3] == 0)
+    for a, c in zip(alone, batch):
+        assert np.array_equal(a, c)
+
+
 def test_empty_frame_gives_zero(ctx):
     f = synth.config2()
     px = f.pixels.astype(np.float32)
