@@ -165,7 +165,9 @@ rsim_status rsim_synth(rsim_ctx* ctx, const rsim_radar_params* params, const rsi
  * (one cudaMemcpyAsync), all on `stream`.  When the pixel arrays are reachable from the
  * device (page-locked memory, or any host memory on a node whose GPU reads pageable
  * memory through the host page tables, as over NVLink-C2C), the kernels read them in
- * place instead of copies; the cube is always staged and copied back in one piece.
+ * place instead of copies.  The cube is always staged and comes back in one piece: into
+ * page-locked memory (16-byte aligned, a whole number of 16-byte units) by a copy kernel
+ * through its mapped address, else by one cudaMemcpyAsync.
  * Either way the results are those of rsim_synth, and the host buffers must stay valid
  * and unchanged until the stream has passed the call's work (e.g. rsim_sync_status); with
  * pageable memory and no direct access the copies block the calling thread.  The staging buffer grows when
