@@ -105,6 +105,28 @@ prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigne
   __shared__ int s_warp[kWarps];
   __shared__ float s_max[kWarps];
 
+  // this thread's pixel fields, loaded before anything waits on them: over a host link
+  // (pixel arrays read in place) their latency then overlaps the offset sum below
+  static_assert(kPrepTile == kPrepThreads, "one pixel per thread");
+  const T* R = (const T*)fr.range;
+  const T* sre = (const T*)fr.sre;
+  const T* sim = (const T*)fr.sim;
+  const T* az = (const T*)fr.az;
+  const T* el = (const T*)fr.el;
+  const T* vel = (const T*)fr.vel;
+  const int64_t p = base + tid;
+  T f_re = T(0), f_im = T(0), f_r = T(0), f_az = T(0), f_el = T(0), f_vel = T(0);
+  if (p < fr.P) {
+    f_re = sre[p];
+    f_im = sim[p];
+    if (!idx_only) {
+      f_r = R[p];
+      f_az = az[p];
+      f_el = el[p];
+      f_vel = vel[p];
+    }
+  }
+
   // offset of this tile = sum of the counts of earlier tiles (fixed order)
   long long part = 0;
   for (int b = tid; b < (int)blockIdx.x; b += kPrepThreads) part += fr.blk_count[b];
@@ -118,18 +140,10 @@ prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigne
   }
   __syncthreads();
   long long off = s_off;
-
-  const T* R = (const T*)fr.range;
-  const T* sre = (const T*)fr.sre;
-  const T* sim = (const T*)fr.sim;
-  const T* az = (const T*)fr.az;
-  const T* el = (const T*)fr.el;
-  const T* vel = (const T*)fr.vel;
   float mymax = 0.f;
 
-  for (int row = 0; row < kPrepTile / kPrepThreads; ++row) {
-    const int64_t p = base + (int64_t)row * kPrepThreads + tid;
-    const bool v = (p < fr.P) && is_valid(sre, sim, p);
+  {
+    const bool v = (p < fr.P) && ((f_re != T(0)) || (f_im != T(0)));  // as is_valid
     const unsigned bal = __ballot_sync(0xffffffffu, v);
     __syncthreads();  // s_warp reuse
     if (lane == 0) s_warp[warp] = __popc(bal);
@@ -144,8 +158,8 @@ prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigne
     if (v) {
       fr.idx[q] = (int32_t)p;
       if (!idx_only) {
-        const double r = (double)R[p], a = (double)az[p], e = (double)el[p], w = (double)vel[p];
-        double s_re = (double)sre[p], s_im = (double)sim[p];
+        const double r = (double)f_r, a = (double)f_az, e = (double)f_el, w = (double)f_vel;
+        double s_re = (double)f_re, s_im = (double)f_im;
         const bool ok = isfinite(r) && r > 0.0 && isfinite(a) && isfinite(e) && isfinite(w) &&
                         isfinite(s_re) && isfinite(s_im);
         uint64_t A0 = 0, dA = 0, G = 0, Bq = 0, Bm = 0;
