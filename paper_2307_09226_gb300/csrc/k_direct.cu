@@ -233,7 +233,7 @@ bool uses_partial(int tier, int64_t P, int splits) {
 }
 
 int group_chunks(int tier) {
-  return (tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16) ? 32 : 96;
+  return (tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16) ? 40 : 96;
 }
 
 int units_per_split(int tier, int V, int Ns, int L) {

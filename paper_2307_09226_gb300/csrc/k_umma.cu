@@ -360,6 +360,17 @@ __device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, cons
   return x;
 }
 
+// Accumulation groups of a unit: its chunks c0 .. c1 - 1 cut into the fewest equal groups
+// of at most `gmax` chunks, one drain each (a unit without chunks still has one group,
+// whose drain writes zeros).  Equal groups spend no drain on a short tail group.
+__device__ __forceinline__ int64_t unit_groups(const Unit& x, int gmax) {
+  const int64_t n = x.c1 - x.c0;
+  return n > 0 ? (n + gmax - 1) / gmax : 1;
+}
+__device__ __forceinline__ int64_t group_begin(const Unit& x, int64_t ngr, int64_t k) {
+  return x.c0 + (x.c1 - x.c0) * k / ngr;
+}
+
 // sigma scale of the FP16 tiers: 2^-e with max(|re|, |im|) * 2^-e in [1/2, 1)
 __device__ __forceinline__ float sigma_scale(const FrameIO& fr, int scaled) {
   if (!scaled) return 1.f;
@@ -525,9 +536,9 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
       const uint32_t* pC = fr.phC + (int64_t)(row_ok ? v : 0) * fr.Pcap;
       const float oscale = 1.f / sigma_scale(fr, scaled);
       const int l0 = x.nt * g.NT;
-      int64_t g0 = x.c0;
-      do {
-        const int64_t g1 = (x.c1 < g0 + g.group) ? x.c1 : g0 + g.group;
+      const int64_t ngr = unit_groups(x, g.group);
+      for (int64_t gk = 0; gk < ngr; ++gk) {
+        const int64_t g0 = group_begin(x, ngr, gk), g1 = group_begin(x, ngr, gk + 1);
         for (int64_t c = g0; c < g1; ++c, ++kk, ++pk) {
           if ((int)(kk & 1u) != group) continue;  // the other group makes this stage
           const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
@@ -629,8 +640,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         fence_before();
         mbar_arrive(&sh->acc_empty);
         ++gi;
-        g0 = g1;
-      } while (g0 < x.c1);
+      }
     }
   } else if (warp == kAWarps) {
     // ------------- MMA issuer (one thread) -------------
@@ -641,9 +651,9 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
       const uint64_t desc0 = sdesc_sw128(smem_u32(bstage));  // hi image of B stage 0
       while (alive && next_unit(sh, ui++, status, &u, false)) {
         const Unit x = decode(g, frames, k, u, rank);
-        int64_t g0 = x.c0;
-        do {
-          const int64_t g1 = (x.c1 < g0 + g.group) ? x.c1 : g0 + g.group;
+        const int64_t ngr = unit_groups(x, g.group);
+        for (int64_t gk = 0; gk < ngr; ++gk) {
+          const int64_t g0 = group_begin(x, ngr, gk), g1 = group_begin(x, ngr, gk + 1);
           if (!mbar_wait(&sh->acc_empty, (gi & 1u) ^ 1u, sh, status)) {
             alive = false;
             break;
@@ -669,8 +679,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           else
             mbar_arrive(&sh->acc_full);
           ++gi;
-          g0 = g1;
-        } while (g0 < x.c1);
+        }
       }
       // every issued MMA completes before tensor memory is released
       mma_commit(&sh->fin);
