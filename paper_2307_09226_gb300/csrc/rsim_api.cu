@@ -295,18 +295,25 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     char* scratch = ws + align_up(frames_bytes(k, Ps.data(), F, splits, tier), 256);
     const size_t slot = align_up(nufft_scratch_bytes(k, mp), 256);
     const int S = nufft_slots(F);
-    if (S > 1 && !ctx->nu_st[0]) {
-      for (int i = 0; i < rsim_ctx::kNuStreams; ++i) {
-        e = cudaStreamCreateWithFlags(&ctx->nu_st[i], cudaStreamNonBlocking);
+    if (S > 1 && !ctx->nu_ready) {
+      // create what is missing (an earlier call may have failed part way)
+      for (cudaStream_t& x : ctx->nu_st) {
+        if (x) continue;
+        e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
         if (e != cudaSuccess) {
-          ctx->nu_st[i] = nullptr;
+          x = nullptr;
           return cuda_fail(e, "cudaStreamCreate (NUFFT streams)");
         }
       }
       for (cudaEvent_t& x : ctx->nu_ev) {
+        if (x) continue;
         e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaEventCreate (NUFFT streams)");
+        if (e != cudaSuccess) {
+          x = nullptr;
+          return cuda_fail(e, "cudaEventCreate (NUFFT streams)");
+        }
       }
+      ctx->nu_ready = true;
     }
     // frame f runs on stream f mod S with scratch slot f mod S; every stream first waits
     // for the compaction and phases on `st`, and `st` then waits for every stream

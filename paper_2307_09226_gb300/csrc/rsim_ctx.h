@@ -28,6 +28,7 @@ struct rsim_ctx {
   static constexpr int kNuStreams = 8;
   cudaStream_t nu_st[kNuStreams] = {};
   cudaEvent_t nu_ev[kNuStreams + 1] = {};  // one per stream, then the fork
+  bool nu_ready = false;                   // all of nu_st and nu_ev exist
   std::mutex plan_mu;
   std::map<std::string, rsim_plan> plans;
   // stage profiling (rsim_profile_enable / rsim_profile_read)
