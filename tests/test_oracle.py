@@ -190,6 +190,61 @@ def test_brute_force_tiny_against_cmath():
                 assert abs(got[v, n, l] - z) < 1e-12 * max(1.0, abs(z))
 
 
+def test_phase_cycles_matches_the_phase_written_out_term_by_term():
+    """phase_cycles against Eq. 1/Eq. 2's phase written out with `math` per pixel, on a
+    frame with a masked pixel (the vector runs over valid pixels, ascending) and with the
+    TDM motion term; exp(j 2 pi phase) summed over p reproduces the literal cube."""
+    from dataclasses import replace
+    rng = np.random.default_rng(11)
+    R = rng.uniform(0.5, 9, 5)
+    sr, si = rng.normal(size=5), rng.normal(size=5)
+    sr[2] = si[2] = 0.0  # background miss
+    az, el, vel = rng.uniform(-1, 1, 5), rng.uniform(-0.5, 0.5, 5), rng.uniform(-3, 3, 5)
+    px = Pixels(R, sr, si, az, el, vel)
+    for tdm in (False, True):
+        radar = replace(Radar(M=2, N=2, Ns=4, L=3, mu=2e14, t_b=1e-4), tdm_motion=tdm)
+        r = radar.resolved()
+        cube = oracle.cube_literal(radar, px)
+        for v in range(4):
+            for n in range(4):
+                for l in range(3):
+                    got = oracle.phase_cycles(radar, px, v, n, l)
+                    want = []
+                    for p in (0, 1, 3, 4):
+                        u = math.cos(el[p]) * math.sin(az[p])
+                        Rv = R[p] + v * r.d_rx * u / 2
+                        ph = (2 * r.mu * Rv / r.c * n / r.fs + v * r.d_rx * u / r.lam
+                              - 2 * vel[p] / r.lam * l * r.t_slow)
+                        if tdm:
+                            ph -= 2 * vel[p] / r.lam * (v // 2) * r.t_b
+                        want.append(ph)
+                    assert got.shape == (4,)
+                    np.testing.assert_allclose(got, want, rtol=0, atol=1e-9)
+                    z = sum(complex(sr[p], si[p]) * cmath.exp(2j * math.pi * w)
+                            for p, w in zip((0, 1, 3, 4), got))
+                    assert abs(cube[v, n, l] - z) < 1e-11 * max(1.0, abs(z))
+
+
+def test_rel_l2_is_the_normwise_relative_error_over_the_whole_cube():
+    """The yardstick of every parity claim, against values worked out by hand."""
+    assert oracle.rel_l2(np.array([3 + 4j]), np.array([0j])) == 5.0  # zero reference: absolute
+    assert oracle.rel_l2(np.array([1 + 1j, 0]), np.array([1, 0])) == 1.0
+    x = np.random.default_rng(0).normal(size=(2, 3, 4)) * (1 + 0.5j)
+    assert oracle.rel_l2(x, x) == 0.0
+    # normwise, not a per-entry mean or maximum: sqrt(0.1^2) / sqrt(1^2 + 10^2)
+    got = oracle.rel_l2(np.array([1.1, 10.0]), np.array([1.0, 10.0]))
+    assert abs(got - 0.1 / math.sqrt(101.0)) < 1e-15
+    assert abs(got - 0.05) > 1e-2 and abs(got - 0.1) > 1e-2
+    # complex entries count as two reals: |(1+2j) - (1+1j)| / |1+1j|
+    assert abs(oracle.rel_l2(np.array([1 + 2j]), np.array([1 + 1j])) - 1 / math.sqrt(2)) < 1e-15
+    assert abs(oracle.rel_l2(np.array([2 + 1j]), np.array([1 + 1j])) - 1 / math.sqrt(2)) < 1e-15
+    # the whole array at once, whatever its shape; not relative to the larger argument
+    a = np.array([[1.0, 2.0], [2.0, 4.0]], dtype=complex)
+    b = np.array([[1.0, 2.0], [2.0, 0.0]], dtype=complex)
+    assert abs(oracle.rel_l2(a, b) - 4.0 / 3.0) < 1e-15
+    assert abs(oracle.rel_l2(b, a) - 4.0 / 5.0) < 1e-15
+
+
 def test_literal_and_separable_agree_on_config1():
     f = synth.config1()
     a = oracle.cube_literal(f.radar, f.pixels)
