@@ -308,6 +308,8 @@ def run_gpu(args):
     usable = []
     for t in tiers:
         try:
+            # every tier runs (and is checked with) the tuned plan of the frame's shape bucket
+            _abi.rsim_autotune(ctx.h, radar, frame.pixels.P, _abi.TIERS[t])
             cube = ctx.synth(radar, px, t)
             st = ctx.sync_status()
         except _abi.RsimError as e:
@@ -414,6 +416,7 @@ def run_gpu(args):
             ("fp16x2+f32acc" if tier == "split_fp16" else "bf16x2+f32acc"),
             "data": "synthetic",
             "config": {"workload": frame.meta["workload"], "tier": tier, "P": radar and frame.pixels.P,
+                       "plan": _abi.rsim_get_plan(ctx.h, radar, frame.pixels.P, _abi.TIERS[tier]).as_dict(),
                        "P_valid": pv, "V": radar.V, "Ns": radar.Ns, "L": radar.L,
                        "path_samples_per_frame": samples, "l2": "flushed between timed steps",
                        "parallelism": f"replicas x{ws}"},
@@ -486,6 +489,13 @@ def run_batch(ctx, tier, steps, warmup):
     pvs = [_valid_count(f.pixels) for f in frames]
     samples = sum(pvs) * radar.V * radar.Ns * radar.L
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    # the batch runs with the tuned plan of its shape bucket (the plan of its largest frame)
+    from paper_2307_09226_gb300 import _abi
+    P = max(f.pixels.P for f in frames)
+    plan = None
+    if tier in _abi.TIERS and tier != "nufft":
+        _abi.rsim_autotune(ctx.h, radar, P, _abi.TIERS[tier])
+        plan = _abi.rsim_get_plan(ctx.h, radar, P, _abi.TIERS[tier]).as_dict()
     for _ in range(warmup):
         ctx.synth_batch(radar, pxs, tier, cubes=cubes)
     torch.cuda.synchronize()
@@ -512,7 +522,7 @@ def run_batch(ctx, tier, steps, warmup):
     b.record()
     torch.cuda.synchronize()
     truth = [f.meta["v_torso"] for f in frames]
-    return {"workload": "walking-64x256x256-V12-Ns256-L128", "tier": tier, "frames": len(frames),
+    return {"workload": "walking-64x256x256-V12-Ns256-L128", "tier": tier, "plan": plan, "frames": len(frames),
             "P_valid_min": min(pvs), "P_valid_max": max(pvs), "ms_per_batch": round(t, 4),
             "value": samples / (t * 1e-3) / 1e9, "unit": "Gpath-samples/s", "steps": steps,
             "doppler_time": {"ms_64_frames": round(a.elapsed_time(b), 4),
@@ -669,12 +679,15 @@ def run_raycast(ctx, tier, steps=10, warmup=3):
                         "speed_m_s": round(scenes[0][1]["speed"], 3)}}
 
 
-def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5):
+def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5, tune_budget_s=45.0):
     """Config 5: Poisson stream of mixed requests (M 2-4, N 4-12, Ns 128-512, L 64-256,
-    64^2..512^2 pixels, FP32 and split-BF16 tiers) into the continuous-batching server at
-    0.7 x the measured capacity: n_warmup requests, a new tally, then n_requests measured;
-    latency is submit -> completion.  The requests cycle over `pool` distinct frames
-    resident on the device (a frame's previous request has finished before it is reused)."""
+    64^2..512^2 pixels, FP32 and split-BF16 tiers) into the continuous-batching server:
+    n_warmup requests, a new tally, then n_requests measured; latency is submit ->
+    completion.  Offered loads 0.5 and 0.7 x the measured capacity with first-fit
+    admission, and 0.7 with shortest-first admission.  The requests cycle over `pool`
+    distinct frames resident on the device (a frame's previous request has finished
+    before it is reused).  Before any timing, the pool's shape buckets are tuned, smallest
+    estimated work first, until tune_budget_s has passed; the rest keep the default plan."""
     import numpy as np
     import torch
     from paper_2307_09226_gb300 import _abi, device, synth
@@ -684,6 +697,23 @@ def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5):
     cubes = [device.cube_tensor(f.radar) for f in frames]
     made = [_abi.make_request(f.radar, px, _abi.TIERS[r["tier"]], cb)
             for r, f, px, cb in zip(reqs, frames, pxs, cubes)]
+    # tune the shape buckets of the pool
+    keys = {}
+    for r, f in zip(reqs, frames):
+        rd = f.radar
+        key = (r["tier"], rd.V, rd.Ns, rd.L, (int(f.pixels.P) - 1).bit_length())
+        work = f.pixels.P * rd.V * rd.Ns * rd.L * (10.0 if r["tier"] == "fp32" else 1.0)
+        keys.setdefault(key, (work, rd, int(f.pixels.P), r["tier"]))
+    t_tune = time.perf_counter()
+    tuned = set()
+    for key, (work, rd, P, tier) in sorted(keys.items(), key=lambda kv: kv[1][0]):
+        if time.perf_counter() - t_tune > tune_budget_s:
+            break
+        _abi.rsim_autotune(ctx.h, rd, P, _abi.TIERS[tier])
+        tuned.add(key)
+    tune_s = time.perf_counter() - t_tune
+    on_tuned = sum(1 for r, f in zip(reqs, frames)
+                   if (r["tier"], f.radar.V, f.radar.Ns, f.radar.L, (int(f.pixels.P) - 1).bit_length()) in tuned)
     # capacity: every pool request once, back to back, on one server slot
     srv = _abi.rsim_server_create(ctx.h, slots=1)
     t0 = time.perf_counter()
@@ -691,42 +721,53 @@ def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5):
         _abi.rsim_server_wait(srv, _abi.rsim_server_submit(srv, m), -1)
     alone_s = (time.perf_counter() - t0) / len(made)
     _abi.rsim_server_destroy(srv)
-    rate = 0.7 / alone_s
     rng = np.random.default_rng(seed + 1)
-    srv = _abi.rsim_server_create(ctx.h, slots=slots)
-    bad = 0
 
-    def stream(n, first):
-        nonlocal bad
-        gaps = rng.exponential(1.0 / rate, n)
-        tickets = {}
-        due = time.perf_counter()
-        for j in range(first, first + n):
-            due += gaps[j - first]
-            prev = tickets.pop(j - pool, None)  # the same frame's previous request
-            if prev is not None:
-                bad += _abi.rsim_server_wait(srv, prev, -1) != _abi.OK
-            delay = due - time.perf_counter()
-            if delay > 0:
-                time.sleep(delay)
-            tickets[j] = _abi.rsim_server_submit(srv, made[j % pool])
-        for t in tickets.values():
-            bad += _abi.rsim_server_wait(srv, t, -1) != _abi.OK
+    def run(load, policy):
+        rate = load / alone_s
+        srv = _abi.rsim_server_create(ctx.h, slots=slots, policy=policy)
+        bad = 0
 
-    stream(n_warmup, 0)
-    _abi.rsim_server_stats_reset(srv)
-    stream(n_requests, n_warmup)
-    st = _abi.rsim_server_stats_get(srv)
-    _abi.rsim_server_destroy(srv)
-    torch.cuda.synchronize()
-    return {"workload": "poisson-mix-M2..4-N4..12-Ns128..512-L64..256-P4k..262k", "requests": int(st.completed),
-            "warmup_requests": n_warmup, "distinct_frames": pool,
-            "slots": slots, "rate_req_s": round(rate, 2), "offered_load": 0.7,
-            "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),
-            "max_ms": round(st.max_ms, 3), "req_per_s": round(st.completed / max(st.busy_s, 1e-9), 2),
-            "value": st.path_samples / max(st.busy_s, 1e-9) / 1e9, "unit": "Gpath-samples/s",
-            "failed": int(st.failed) + bad, "peak_in_flight": int(st.peak_in_flight),
-            "alone_mean_ms": round(alone_s * 1e3, 3)}
+        def stream(n, first):
+            nonlocal bad
+            gaps = rng.exponential(1.0 / rate, n)
+            tickets = {}
+            due = time.perf_counter()
+            for j in range(first, first + n):
+                due += gaps[j - first]
+                prev = tickets.pop(j - pool, None)  # the same frame's previous request
+                if prev is not None:
+                    bad += _abi.rsim_server_wait(srv, prev, -1) != _abi.OK
+                delay = due - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                tickets[j] = _abi.rsim_server_submit(srv, made[j % pool])
+            for t in tickets.values():
+                bad += _abi.rsim_server_wait(srv, t, -1) != _abi.OK
+
+        stream(n_warmup, 0)
+        _abi.rsim_server_stats_reset(srv)
+        stream(n_requests, n_warmup)
+        st = _abi.rsim_server_stats_get(srv)
+        _abi.rsim_server_destroy(srv)
+        torch.cuda.synchronize()
+        return {"offered_load": load, "policy": policy, "rate_req_s": round(rate, 2), "requests": int(st.completed),
+                "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),
+                "max_ms": round(st.max_ms, 3), "p99_queue_ms": round(st.p99_queue_ms, 3),
+                "max_queue_ms": round(st.max_queue_ms, 3), "overtakes": int(st.overtakes),
+                "req_per_s": round(st.completed / max(st.busy_s, 1e-9), 2),
+                "value": st.path_samples / max(st.busy_s, 1e-9) / 1e9, "unit": "Gpath-samples/s",
+                "failed": int(st.failed) + bad, "peak_in_flight": int(st.peak_in_flight)}
+
+    runs = [run(0.7, "first_fit"), run(0.5, "first_fit"), run(0.7, "shortest_first")]
+    head = dict(runs[0])
+    head.update({"workload": "poisson-mix-M2..4-N4..12-Ns128..512-L64..256-P4k..262k",
+                 "warmup_requests": n_warmup, "distinct_frames": pool, "slots": slots, "age_limit_ms": 100,
+                 "alone_mean_ms": round(alone_s * 1e3, 3),
+                 "tuning": {"buckets": len(keys), "tuned": len(tuned), "requests_on_tuned_plans": on_tuned,
+                            "pool": pool, "seconds": round(tune_s, 1)},
+                 "by_load_and_policy": runs})
+    return head
 
 
 def main():

@@ -358,53 +358,87 @@ typedef struct {
 rsim_status rsim_profile_enable(rsim_ctx* ctx, int32_t on);
 rsim_status rsim_profile_read(rsim_ctx* ctx, rsim_profile* out);
 
-/* Kernel-launch plan chosen for a shape (what the autotuner decides). */
+/* Kernel-launch plan of a shape: the tile shapes and the work split that the autotuner
+ * decides.  Plans are kept per shape bucket: (tier, V = M N, N_s, L, ceil(log2 P)), so
+ * frames and requests whose pixel counts lie in the same power-of-two range share one
+ * plan.  Without a tuned or pinned plan for its bucket, a shape gets the default rule
+ * (tile_n and group_chunks at their defaults, splits from the exact P).  A plan never
+ * depends on the data or on the load, so the same frame always runs the same kernels
+ * with the same summation order. */
 typedef struct {
-  int32_t splits;        /* pixel splits of the contraction (K-split) */
-  int32_t chunk_px;      /* pixels per pipeline stage */
-  int32_t grid;          /* CTAs of the contraction launch */
-  int32_t variant;       /* kernel variant id (tier specific) */
-  int32_t tuned;         /* 1 if chosen by timing, 0 if by the default rule */
-  int32_t reserved[3];
+  int32_t splits;        /* pixel splits of the contraction (K-split), 1..64 */
+  int32_t chunk_px;      /* pixels per pipeline stage (always 32; reported) */
+  int32_t grid;          /* CTAs of the persistent tensor-core contraction, 0 = one per SM */
+  int32_t variant;       /* reserved: must be 0 */
+  int32_t tuned;         /* 1 if chosen by timing, 0 if by the default rule or pinned */
+  int32_t tile_n;        /* tile shape.  Tensor-core tiers: l values per column tile, NT,
+                            a multiple of 8 in 8..128 and at most L rounded up to 8 (the
+                            MMA's N is 2 NT; default min(128, L rounded up to 8)).  FP32
+                            tier: n values per CTA tile, 64 or 128 (default 128); the CTA
+                            tile is tile_n x 64 (l).  NUFFT tier: ignored.  0 = default */
+  int32_t group_chunks;  /* tensor-core tiers: 32-pixel chunks summed in one tensor-memory
+                            accumulator before it is drained into round-to-nearest FP32
+                            sums.  The accumulator rounds toward zero, so the cap bounds the
+                            error: 1..40 for split tiers (default 40), 1..384 for plain
+                            16-bit tiers (default 96).  Other tiers: ignored.  0 = default */
+  int32_t reserved;
 } rsim_plan;
 
-/* Time candidate plans for (params, P, tier) on `stream` with synthetic pixels and keep
- * the fastest in the context's cache (and in the JSON file named by the RSIM_TUNE_CACHE
- * environment variable, if set).  The choice depends on the shape only.  Synchronous.
+/* Time candidate plans for the bucket of (params, P, tier) on `stream` with synthetic
+ * full-valid pixels of count P, and keep the fastest for the bucket in the context's cache
+ * (and in the JSON file named by the RSIM_TUNE_CACHE environment variable, if set).
+ * Candidates: the split count around the default rule, the contraction's CTA count,
+ * the column tile NT (tensor tiers) or the n tile (FP32), and the accumulation-group
+ * length (tensor tiers, never above the accuracy caps of rsim_plan).  The choice
+ * depends on the shape only.  Synchronous; allocates scratch with cudaMalloc.
  * Errors: as rsim_synth. */
 rsim_status rsim_autotune(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
                           rsim_tier tier, rsim_plan* chosen, rsim_stream stream);
 
-/* Pin the plan for (params, P, tier) in the context's cache (replaces a tuned or default
- * plan).  plan->splits in 1..64; plan->grid 0 (one CTA per SM) or a positive CTA count.
- * Host only.  Errors: INVALID_ARG. */
+/* Pin `plan` for the bucket of (params, P, tier) in the context's cache (replaces a tuned
+ * or default plan).  splits in 1..64; grid 0 (one CTA per SM) or a positive CTA count
+ * (more than the SM count runs as one per SM); variant 0; tile_n and group_chunks 0 or in
+ * the ranges stated in rsim_plan.  Host only.  Errors: INVALID_ARG. */
 rsim_status rsim_set_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
                           rsim_tier tier, const rsim_plan* plan);
 
-/* The plan rsim_synth would use now for (params, P, tier).  Host only. */
+/* The plan rsim_synth would use now for (params, P, tier), with tile_n and group_chunks
+ * resolved (never 0 for the tiers that use them).  Host only. */
 rsim_status rsim_get_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
                           rsim_tier tier, rsim_plan* plan);
 
 /* ----------------------------------------------------------------------------------
  * Serving: continuous batching of cube-synthesis requests.
  *
- * A server owns `slots` CUDA streams, each with its own workspace.  submit() queues a
- * request (FIFO); a host scheduler thread admits the head request as soon as a slot is
- * free and its workspace fits in the HBM budget still unreserved, and launches it on
- * that slot's stream, so requests that arrive while others run start as soon as
- * resources free up and their kernels overlap on the device.  A request whose estimated
- * device time (path-samples at its tier's nominal rate) is under 2 ms runs on the slot's
- * high-priority stream, so its blocks start ahead of long requests' pending blocks; the
- * others run at low priority.  Results do not depend on the priority.  Completion is
- * detected by a host function after the request's work; latency is measured from
- * submit() to completion.
+ * A server owns `slots` slots, each with two CUDA streams and its own workspace.
+ * submit() queues a request; a host scheduler thread admits queued requests as soon as a
+ * slot is free and the request's workspace fits in the HBM budget still unreserved, and
+ * launches each on its slot's stream, so requests that arrive while others run start as
+ * soon as resources free up and their kernels overlap on the device.
+ *
+ * Which queued request goes next (rsim_server_opts.policy): RSIM_SERVE_FIRST_FIT takes
+ * the oldest request that fits (a request too large for the free budget does not hold
+ * back smaller ones behind it); RSIM_SERVE_SHORTEST_FIRST takes, among those that fit,
+ * the one with the least estimated device time (path-samples at its tier's nominal rate;
+ * oldest first among equals).  Either way a request may be passed over only until it has
+ * waited age_limit_ms since its submission: from then on the oldest such request goes
+ * next and nothing overtakes it, so no request starves.  A request whose estimated device
+ * time is under 2 ms runs on the slot's high-priority stream, so its blocks start ahead
+ * of long requests' pending blocks; the others run at low priority.  Results do not
+ * depend on the policy or the priority.  Completion is detected by a host function after
+ * the request's work; latency is measured from submit() to completion.
  * ---------------------------------------------------------------------------------- */
 typedef struct rsim_server rsim_server;
+
+enum { RSIM_SERVE_FIRST_FIT = 0, RSIM_SERVE_SHORTEST_FIRST = 1 };
 
 typedef struct {
   int32_t slots;             /* concurrent requests on the device (>= 1) */
   int32_t max_queue;         /* queued requests accepted before submit() refuses (BUDGET) */
   size_t hbm_budget_bytes;   /* bound on the sum of admitted workspaces (0 = no bound) */
+  int32_t policy;            /* RSIM_SERVE_FIRST_FIT (0) or RSIM_SERVE_SHORTEST_FIRST */
+  int32_t age_limit_ms;      /* a queued request may be overtaken until it has waited this
+                                long (0 selects 100 ms; < 0: never overtaken, strict FIFO) */
 } rsim_server_opts;
 
 typedef struct {
@@ -423,6 +457,8 @@ typedef struct {
   size_t peak_reserved_bytes;               /* largest sum of admitted workspaces seen */
   int32_t peak_in_flight;                   /* largest number of concurrently running requests */
   int32_t reserved;
+  double p99_queue_ms, max_queue_ms;        /* submit -> admission wait of completed requests */
+  uint64_t overtakes;                       /* admissions that passed over an older queued request */
 } rsim_server_stats;
 
 rsim_status rsim_server_create(rsim_ctx* ctx, const rsim_server_opts* opts, rsim_server** out);

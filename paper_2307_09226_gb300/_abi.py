@@ -78,11 +78,21 @@ RC_NO_FALLOFF = 1
 
 class rsim_plan(Structure):
     _fields_ = [("splits", c_int32), ("chunk_px", c_int32), ("grid", c_int32),
-                ("variant", c_int32), ("tuned", c_int32), ("reserved", c_int32 * 3)]
+                ("variant", c_int32), ("tuned", c_int32), ("tile_n", c_int32),
+                ("group_chunks", c_int32), ("reserved", c_int32)]
+
+    def as_dict(self) -> dict:
+        return {"splits": self.splits, "grid": self.grid, "tile_n": self.tile_n,
+                "group_chunks": self.group_chunks, "tuned": bool(self.tuned)}
+
+
+SERVE_FIRST_FIT, SERVE_SHORTEST_FIRST = 0, 1
+SERVE_POLICIES = {"first_fit": SERVE_FIRST_FIT, "shortest_first": SERVE_SHORTEST_FIRST}
 
 
 class rsim_server_opts(Structure):
-    _fields_ = [("slots", c_int32), ("max_queue", c_int32), ("hbm_budget_bytes", c_size_t)]
+    _fields_ = [("slots", c_int32), ("max_queue", c_int32), ("hbm_budget_bytes", c_size_t),
+                ("policy", c_int32), ("age_limit_ms", c_int32)]
 
 
 class rsim_request(Structure):
@@ -95,7 +105,8 @@ class rsim_server_stats(Structure):
                 ("failed", c_uint64), ("p50_ms", c_double), ("p99_ms", c_double),
                 ("mean_ms", c_double), ("max_ms", c_double), ("busy_s", c_double),
                 ("path_samples", c_double), ("peak_reserved_bytes", c_size_t),
-                ("peak_in_flight", c_int32), ("reserved", c_int32)]
+                ("peak_in_flight", c_int32), ("reserved", c_int32), ("p99_queue_ms", c_double),
+                ("max_queue_ms", c_double), ("overtakes", c_uint64)]
 
 
 class rsim_profile(Structure):
@@ -360,8 +371,9 @@ def rsim_profile_read(ctx) -> rsim_profile:
     return p
 
 
-def rsim_set_plan(ctx, radar, P: int, tier: int, splits: int, grid: int = 0, variant: int = 0):
-    plan = rsim_plan(int(splits), 32, int(grid), int(variant), 1)
+def rsim_set_plan(ctx, radar, P: int, tier: int, splits: int, grid: int = 0, tile_n: int = 0,
+                  group_chunks: int = 0, variant: int = 0):
+    plan = rsim_plan(int(splits), 32, int(grid), int(variant), 0, int(tile_n), int(group_chunks), 0)
     check(load().rsim_set_plan(ctx, ctypes.byref(radar_params(radar)), int(P), int(tier),
                                ctypes.byref(plan)))
 
@@ -373,9 +385,11 @@ def rsim_get_plan(ctx, radar, P: int, tier: int) -> rsim_plan:
     return plan
 
 
-def rsim_server_create(ctx, slots=4, max_queue=4096, hbm_budget_bytes=0) -> c_void_p:
+def rsim_server_create(ctx, slots=4, max_queue=4096, hbm_budget_bytes=0, policy="first_fit",
+                       age_limit_ms=0) -> c_void_p:
     h = c_void_p()
-    opts = rsim_server_opts(int(slots), int(max_queue), int(hbm_budget_bytes))
+    opts = rsim_server_opts(int(slots), int(max_queue), int(hbm_budget_bytes), SERVE_POLICIES[policy],
+                            int(age_limit_ms))
     check(load().rsim_server_create(ctx, ctypes.byref(opts), ctypes.byref(h)))
     return h
 

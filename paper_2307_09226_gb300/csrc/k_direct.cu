@@ -4,11 +4,12 @@
 // slow-time part b_p l, so each cube entry is
 //     cube[v][n][l] = sum_q G_v[q][n] * D[q][l],
 //     G_v[q][n] = exp(j 2 pi (a_{q,v} n + c_{q,v})),   D[q][l] = sigma_q exp(j 2 pi b_q l),
-// over the compacted valid pixels q.  A CTA owns a 64 (n) x 64 (l) tile of one
-// channel and one contiguous split of the pixels; per 32-pixel chunk it writes the
-// chunk's phasors to shared memory (phases are exact 32-bit fixed-point products,
-// so only a phase in [-1/2, 1/2) cycle is ever converted to float) and then every
-// thread accumulates a 4 x 4 block of complex outputs with 4 FFMA per term.
+// over the compacted valid pixels q.  A CTA owns a TN (n) x 64 (l) tile of one channel
+// and one contiguous split of the pixels, TN = 128 or 64 (a plan's tile shape); per
+// 32-pixel chunk it writes the chunk's phasors to shared memory (phases are exact 32-bit
+// fixed-point products, so only a phase in [-1/2, 1/2) cycle is ever converted to float)
+// and then every thread accumulates a (TN / 16) x 4 block of complex outputs with 4 FFMA
+// per term.
 #include <algorithm>
 
 #include "rsim_internal.h"
@@ -16,7 +17,6 @@
 namespace rsim {
 namespace {
 
-constexpr int kTN = 128;      // n per tile
 constexpr int kTL = 64;       // l per tile
 constexpr int kThreads = 256;
 
@@ -39,14 +39,15 @@ __device__ __forceinline__ void cmac(float2& acc, float2 g, float2 d) {
 
 // Phasor tiles of one 32-pixel chunk: G[q][n] = e^{j 2 pi (a n + c)} (channel v),
 // D[q][l] = sigma e^{j 2 pi b l}; zero outside the frame / the cube.
-__device__ __forceinline__ void fill_chunk(float2 (*Gs)[kTN], float2 (*Ds)[kTL], const FrameIO& fr,
+template <int TN>
+__device__ __forceinline__ void fill_chunk(float2 (*Gs)[TN], float2 (*Ds)[kTL], const FrameIO& fr,
                                            const uint32_t* pA, const uint32_t* pC, int64_t q0,
                                            int64_t pv, int n0, int l0, const Consts& k) {
   const int tid = threadIdx.x;
 #pragma unroll
-  for (int i = 0; i < (kChunkPx * kTN) / kThreads; ++i) {
+  for (int i = 0; i < (kChunkPx * TN) / kThreads; ++i) {
     const int e = tid + i * kThreads;
-    const int qq = e / kTN, nn = e % kTN;
+    const int qq = e / TN, nn = e % TN;
     const int64_t q = q0 + qq;
     const int n = n0 + nn;
     float2 g = make_float2(0.f, 0.f);
@@ -69,12 +70,14 @@ __device__ __forceinline__ void fill_chunk(float2 (*Gs)[kTN], float2 (*Ds)[kTL],
   }
 }
 
-// One CTA: a 128 (n) x 64 (l) tile of one channel over one pixel split.  Each thread
-// owns 8 n x 4 l complex outputs; the phasor tiles are double-buffered so that the next
-// chunk is filled before the barrier that hands it over.
+// One CTA: a TN (n) x 64 (l) tile of one channel over one pixel split.  Each thread
+// owns MI = TN / 16 n x 4 l complex outputs; the phasor tiles are double-buffered so that
+// the next chunk is filled before the barrier that hands it over.
+template <int TN>
 __global__ void __launch_bounds__(kThreads, 2)
 direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_per_frame,
            int out_dtype) {
+  constexpr int MI = TN / 16;
   wait_prior_grid();
   const int f = blockIdx.x / units_per_frame;
   int r = blockIdx.x % units_per_frame;
@@ -82,53 +85,53 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
   const int s = r % splits;
   r /= splits;
   const int ntl = (k.L + kTL - 1) / kTL;
-  const int ntn = (k.Ns + kTN - 1) / kTN;
+  const int ntn = (k.Ns + TN - 1) / TN;
   const int tl_i = r % ntl;
   r /= ntl;
   const int tn_i = r % ntn;
   const int v = r / ntn;
-  const int n0 = tn_i * kTN, l0 = tl_i * kTL;
+  const int n0 = tn_i * TN, l0 = tl_i * kTL;
 
   const int64_t pv = (int64_t)fr.meta[0];
   const int64_t nch = (pv + kChunkPx - 1) / kChunkPx;
   const int64_t c0 = nch * s / splits, c1 = nch * (s + 1) / splits;
 
-  extern __shared__ float2 dsm[];  // 2 x (G [32][128] + D [32][64])
-  constexpr int kBuf = kChunkPx * (kTN + kTL);
-  auto gbuf = [&](int b) { return reinterpret_cast<float2 (*)[kTN]>(dsm + b * kBuf); };
-  auto dbuf = [&](int b) { return reinterpret_cast<float2 (*)[kTL]>(dsm + b * kBuf + kChunkPx * kTN); };
+  extern __shared__ float2 dsm[];  // 2 x (G [32][TN] + D [32][64])
+  constexpr int kBuf = kChunkPx * (TN + kTL);
+  auto gbuf = [&](int b) { return reinterpret_cast<float2 (*)[TN]>(dsm + b * kBuf); };
+  auto dbuf = [&](int b) { return reinterpret_cast<float2 (*)[kTL]>(dsm + b * kBuf + kChunkPx * TN); };
 
   const int tid = threadIdx.x;
-  const int tn = tid >> 4, tl = tid & 15;  // rows tn*8 .. +7 ; cols tl + 16 j
-  float2 acc[8][4];
+  const int tn = tid >> 4, tl = tid & 15;  // rows tn*MI .. +MI-1 ; cols tl + 16 j
+  float2 acc[MI][4];
 #pragma unroll
-  for (int i = 0; i < 8; ++i)
+  for (int i = 0; i < MI; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = make_float2(0.f, 0.f);
 
   const uint32_t* pA = fr.phA + (int64_t)v * fr.Pcap;
   const uint32_t* pC = fr.phC + (int64_t)v * fr.Pcap;
 
-  if (c0 < c1) fill_chunk(gbuf(0), dbuf(0), fr, pA, pC, c0 * kChunkPx, pv, n0, l0, k);
+  if (c0 < c1) fill_chunk<TN>(gbuf(0), dbuf(0), fr, pA, pC, c0 * kChunkPx, pv, n0, l0, k);
   __syncthreads();
   for (int64_t c = c0; c < c1; ++c) {
     const int b = (int)((c - c0) & 1);
-    if (c + 1 < c1) fill_chunk(gbuf(b ^ 1), dbuf(b ^ 1), fr, pA, pC, (c + 1) * kChunkPx, pv, n0, l0, k);
-    const float2 (*G)[kTN] = gbuf(b);
+    if (c + 1 < c1) fill_chunk<TN>(gbuf(b ^ 1), dbuf(b ^ 1), fr, pA, pC, (c + 1) * kChunkPx, pv, n0, l0, k);
+    const float2 (*G)[TN] = gbuf(b);
     const float2 (*D)[kTL] = dbuf(b);
 #pragma unroll 2
     for (int qq = 0; qq < kChunkPx; ++qq) {
-      float2 g[8], d[4];
+      float2 g[MI], d[4];
 #pragma unroll
-      for (int i = 0; i < 8; i += 2) {
-        const float4 t = *reinterpret_cast<const float4*>(&G[qq][tn * 8 + i]);
+      for (int i = 0; i < MI; i += 2) {
+        const float4 t = *reinterpret_cast<const float4*>(&G[qq][tn * MI + i]);
         g[i] = make_float2(t.x, t.y);
         g[i + 1] = make_float2(t.z, t.w);
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j) d[j] = D[qq][tl + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 8; ++i)
+      for (int i = 0; i < MI; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) cmac(acc[i][j], g[i], d[j]);
     }
@@ -138,8 +141,8 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
   // write the tile: final cube when there is one split, else this split's partial
   const int64_t rows = (int64_t)k.V * k.Ns;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int n = n0 + tn * 8 + i;
+  for (int i = 0; i < MI; ++i) {
+    const int n = n0 + tn * MI + i;
     if (n >= k.Ns) continue;
     const int64_t row = (int64_t)v * k.Ns + n;
 #pragma unroll
@@ -199,18 +202,28 @@ __global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, 
 
 }  // namespace
 
-cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits,
-                          int out_dtype, cudaStream_t st) {
-  const int ntn = (k.Ns + kTN - 1) / kTN, ntl = (k.L + kTL - 1) / kTL;
+namespace {
+template <int TN>
+cudaError_t launch_direct_t(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
+                            cudaStream_t st) {
+  const int ntn = (k.Ns + TN - 1) / TN, ntl = (k.L + kTL - 1) / kTL;
   const int64_t upf = (int64_t)k.V * ntn * ntl * splits;
   const int64_t blocks = upf * F;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-  const int smem = (int)sizeof(float2) * 2 * kChunkPx * (kTN + kTL);
-  cudaError_t e = cudaFuncSetAttribute(direct_sum, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int smem = (int)sizeof(float2) * 2 * kChunkPx * (TN + kTL);
+  cudaError_t e = cudaFuncSetAttribute(direct_sum<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  return launch_dependent(direct_sum, dim3((unsigned)blocks), dim3(kThreads), (size_t)smem, st, frames, k, splits,
-                          (int)upf, out_dtype);
+  return launch_dependent(direct_sum<TN>, dim3((unsigned)blocks), dim3(kThreads), (size_t)smem, st, frames, k,
+                          splits, (int)upf, out_dtype);
+}
+}  // namespace
+
+cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits, int tile_n,
+                          int out_dtype, cudaStream_t st) {
+  if (tile_n == 64) return launch_direct_t<64>(k, frames, F, splits, out_dtype, st);
+  if (tile_n == 128) return launch_direct_t<128>(k, frames, F, splits, out_dtype, st);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
@@ -224,28 +237,35 @@ cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int spl
                           scale_mode != 0.f ? 1 : 0);
 }
 
-bool uses_partial(int tier, int64_t P, int splits) {
+bool uses_partial(int tier, int64_t P, int splits, int group) {
   if (tier == RSIM_TIER_NUFFT) return false;
   if (splits > 1) return true;
   if (tier == RSIM_TIER_FP32) return false;
   const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
-  return chunks > group_chunks(tier);
+  return chunks > group;
 }
 
 int group_chunks(int tier) {
   return (tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16) ? 40 : 96;
 }
 
-int units_per_split(int tier, int V, int Ns, int L) {
-  if (tier == RSIM_TIER_FP32) return V * ((Ns + kTN - 1) / kTN) * ((L + kTL - 1) / kTL);
+// The split tiers' 2e-5 bar leaves room for the round-toward-zero bias of at most 40
+// chunks (480 accumulating MMAs, a relative shrink of about 1e-5); the plain 16-bit tiers
+// (1e-2) allow 384 chunks (1536 MMAs, about 3e-5).
+int group_chunks_max(int tier) {
+  return (tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16) ? 40 : 384;
+}
+
+int units_per_split(int tier, int V, int Ns, int L, int tile_n) {
+  if (tier == RSIM_TIER_FP32) return V * ((Ns + tile_n - 1) / tile_n) * ((L + kTL - 1) / kTL);
   const int64_t rows = (int64_t)V * Ns;
-  const int nt = (L + 127) / 128;
+  const int nt = (L + tile_n - 1) / tile_n;
   return (int)(((rows + 127) / 128) * nt);
 }
 
-int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms) {
+int default_splits(int tier, int V, int Ns, int L, int tile_n, int64_t P, int num_sms) {
   if (tier == RSIM_TIER_NUFFT) return 1;
-  const int tiles = units_per_split(tier, V, Ns, L);
+  const int tiles = units_per_split(tier, V, Ns, L, tile_n);
   const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
   // keep at least 8 chunks (256 pixels) per split
   int64_t smax = chunks / 8 > 0 ? chunks / 8 : 1;
@@ -285,6 +305,43 @@ int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms) {
     }
   }
   return bs;
+}
+
+void resolve_tile(int tier, const Consts& k, rsim_plan* p) {
+  if (tier == RSIM_TIER_FP32) {
+    if (p->tile_n == 0) p->tile_n = kDirectTileN;
+    p->group_chunks = 0;
+  } else if (tensor_tier(tier)) {
+    if (p->tile_n == 0) p->tile_n = tile_nt(k.L);
+    if (p->group_chunks == 0) p->group_chunks = group_chunks(tier);
+  } else {
+    p->tile_n = 0;
+    p->group_chunks = 0;
+  }
+  p->chunk_px = kChunkPx;
+}
+
+rsim_plan default_plan(int tier, const Consts& k, int64_t P, int num_sms) {
+  rsim_plan p{};
+  resolve_tile(tier, k, &p);
+  p.splits = default_splits(tier, k.V, k.Ns, k.L, p.tile_n, P, num_sms);
+  return p;
+}
+
+std::string plan_problem(int tier, const Consts& k, const rsim_plan& p) {
+  if (p.splits < 1 || p.splits > kMaxSplits) return "plan splits must be in 1..64";
+  if (p.grid < 0) return "plan grid must be >= 0";
+  if (p.variant != 0) return "plan variant must be 0";
+  if (tier == RSIM_TIER_FP32) {
+    if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128) return "FP32 tile_n must be 64 or 128";
+  } else if (tensor_tier(tier)) {
+    const int lmax = std::max(8, (k.L + 7) / 8 * 8);
+    if (p.tile_n != 0 && (p.tile_n < 8 || p.tile_n > 128 || p.tile_n % 8 != 0 || p.tile_n > lmax))
+      return "tensor-core tile_n must be a multiple of 8 in 8..min(128, L rounded up to 8)";
+    if (p.group_chunks < 0 || p.group_chunks > group_chunks_max(tier))
+      return "group_chunks must be in 1.." + std::to_string(group_chunks_max(tier)) + " for this tier";
+  }
+  return std::string();
 }
 
 }  // namespace rsim

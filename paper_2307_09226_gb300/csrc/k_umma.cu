@@ -63,8 +63,7 @@ struct PixStage {
 
 struct Shared {
   uint64_t full[kStages];    // the stage's A (producer arrivals) and B (bulk-copy bytes) are in place
-  uint64_t empty[kStages];   // this CTA's MMAs are done with the stage (it may be rewritten)
-  uint64_t bempty[kStages];  // clusters: every CTA of the cluster is done with the B stage
+  uint64_t empty[kStages];   // the MMAs are done with the stage (it may be rewritten)
   uint64_t pix_full[kPixStages];
   uint64_t pix_empty[kPixStages];
   uint64_t unit_full[kUnitSlots];
@@ -149,36 +148,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-// Multicast form: the bytes land at the same offset in every CTA of `mask` and
-// complete the transaction count of the barrier at the same offset there.
-__device__ __forceinline__ void bulk_g2s_mc(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                            uint16_t mask) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], "
-      "%2, [%3], %4;" ::"r"(smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "h"(mask)
-      : "memory");
-}
-
-__device__ __forceinline__ uint32_t cluster_rank() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_id() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ uint32_t cluster_count() {
-  uint32_t r;
-  asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-  return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -253,16 +222,6 @@ __device__ __forceinline__ void mma_stage<1>(uint32_t d, uint32_t a, uint64_t bd
       : "memory");
 }
 
-// Arrive once on the barrier at the same offset in every CTA of `mask` when this
-// thread's prior tcgen05 operations complete.
-__device__ __forceinline__ void mma_commit_mc(uint64_t* b, uint16_t mask) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-          smem_u32(b)),
-      "h"(mask)
-      : "memory");
-}
-
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                    smem_u32(b))
@@ -323,9 +282,7 @@ __device__ __forceinline__ void split2(float x, float y, uint32_t& hi, uint32_t&
 
 struct Geo {
   int mtiles, ntiles, NT, splits, upf, group, direct, F;
-  int cs;                // CTAs per cluster: consecutive row tiles sharing one B stream
-  int mgroups;           // groups of cs row tiles
-  int64_t total_units;   // cluster work units (frame, row-tile group, column tile, split)
+  int64_t total_units;   // work units (frame, row tile, column tile, split)
   int64_t sstride;       // complex elements of one split's tiled partial sums
   const int32_t* order;  // frames by decreasing valid-pixel count
 };
@@ -336,18 +293,16 @@ struct Unit {
   int v_first, span;
 };
 
-__device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, const Consts& k,
-                                       int64_t u, int rank) {
+__device__ __forceinline__ Unit decode(const Geo& g, const FrameIO* frames, const Consts& k, int64_t u) {
   Unit x;
   x.f = g.order ? g.order[u / g.upf] : (int)(u / g.upf);
-  // row-tile group fastest: the CTAs running at the same time share a pixel range and
-  // so the same slow-time operand images in L2
+  // row tile fastest: the CTAs running at the same time share a pixel range and so the
+  // same slow-time operand images in L2
   int r = (int)(u % g.upf);
-  const int mg = r % g.mgroups;
-  r /= g.mgroups;
+  x.mt = r % g.mtiles;
+  r /= g.mtiles;
   x.nt = r % g.ntiles;
   x.s = r / g.ntiles;
-  x.mt = mg * g.cs + rank;  // may be past the last tile: a CTA that only helps load B
   x.pv = (int64_t)frames[x.f].meta[0];
   const int64_t nch = (x.pv + kChunkPx - 1) / kChunkPx;
   x.c0 = nch * x.s / g.splits;
@@ -475,14 +430,11 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   const int N = 2 * g.NT;
   const uint32_t idesc = idesc_f16(BF, N);
   const uint32_t part = (uint32_t)(2 * g.NT * 128);
-  const int rank = g.cs > 1 ? (int)cluster_rank() : 0;
-  const uint16_t cmask = (uint16_t)((1u << g.cs) - 1u);
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < kStages; ++i) {
       mbar_init(&sh->full[i], 32 * kAGroupWarps + 1);  // one producer group + the B loader
       mbar_init(&sh->empty[i], 1);
-      mbar_init(&sh->bempty[i], g.cs);
     }
     for (int i = 0; i < kPixStages; ++i) {
       mbar_init(&sh->pix_full[i], 1);
@@ -508,7 +460,6 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   fence_before();
   __syncthreads();
   fence_after();
-  if (g.cs > 1) cluster_sync();  // peers' barriers are initialised before any multicast
   wait_prior_grid();  // the set-up above overlaps the operand builder's last blocks
   const uint32_t tmem = sh->tmem_base;
   const int64_t rows_total = (int64_t)k.V * k.Ns;
@@ -524,7 +475,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
     long long u;
     bool alive = true;
     while (alive && next_unit(sh, ui++, status, &u, true)) {
-      const Unit x = decode(g, frames, k, u, rank);
+      const Unit x = decode(g, frames, k, u);
       const FrameIO& fr = frames[x.f];
       const int64_t gr = (int64_t)x.mt * 128 + r;
       const bool row_ok = gr < rows_total;
@@ -650,7 +601,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
       bool alive = true;
       const uint64_t desc0 = sdesc_sw128(smem_u32(bstage));  // hi image of B stage 0
       while (alive && next_unit(sh, ui++, status, &u, false)) {
-        const Unit x = decode(g, frames, k, u, rank);
+        const Unit x = decode(g, frames, k, u);
         const int64_t ngr = unit_groups(x, g.group);
         for (int64_t gk = 0; gk < ngr; ++gk) {
           const int64_t g0 = group_begin(x, ngr, gk), g1 = group_begin(x, ngr, gk + 1);
@@ -671,7 +622,6 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
                              idesc, accum);
             accum = 1;
             mma_commit(&sh->empty[st]);
-            if (g.cs > 1) mma_commit_mc(&sh->bempty[st], cmask);
           }
           if (!alive) break;
           if (g1 > g0)
@@ -690,17 +640,14 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
     if (lane == 0) {
       uint32_t pk = 0;
       for (uint32_t ui = 0;; ++ui) {
-        // one CTA: units from the device counter; clusters: a fixed round-robin, so
-        // every CTA of a cluster works on the same unit without exchanging ids
-        const long long uu = g.cs > 1 ? (long long)cluster_id() + (long long)ui * cluster_count()
-                                      : (long long)atomicAdd(unit_counter, 1);
+        const long long uu = (long long)atomicAdd(unit_counter, 1);
         const long long u = uu < g.total_units ? uu : -1;
         const uint32_t slot = ui % kUnitSlots, uph = (ui / kUnitSlots) & 1u;
         if (!mbar_wait(&sh->unit_empty[slot], uph ^ 1u, sh, status)) break;
         *(volatile long long*)&sh->unit[slot] = u;
         mbar_arrive(&sh->unit_full[slot]);
         if (u < 0) break;
-        const Unit x = decode(g, frames, k, u, rank);
+        const Unit x = decode(g, frames, k, u);
         const FrameIO& fr = frames[x.f];
         const bool staged = x.span <= kMaxCh;
         bool alive = true;
@@ -732,25 +679,19 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
       long long u;
       bool alive = true;
       while (alive && next_unit(sh, ui++, status, &u, false)) {
-        const Unit x = decode(g, frames, k, u, rank);
+        const Unit x = decode(g, frames, k, u);
         const FrameIO& fr = frames[x.f];
         for (int64_t c = x.c0; c < x.c1; ++c, ++kk) {
           const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-          if (!mbar_wait(g.cs > 1 ? &sh->bempty[st] : &sh->empty[st], ph ^ 1u, sh, status)) {
+          if (!mbar_wait(&sh->empty[st], ph ^ 1u, sh, status)) {
             alive = false;
             break;
           }
           const unsigned char* src = fr.bimg + ((int64_t)x.nt * fr.bimg_nch + c) * 2 * part;
           unsigned char* dst = bstage + st * kStageBytes;
           mbar_expect_tx(&sh->full[st], SPLIT ? 2 * part : part);
-          if (g.cs > 1) {
-            const uint32_t slice = part / g.cs, off = slice * rank;
-            bulk_g2s_mc(dst + off, src + off, slice, &sh->full[st], cmask);
-            if (SPLIT) bulk_g2s_mc(dst + kBBytes + off, src + part + off, slice, &sh->full[st], cmask);
-          } else {
-            bulk_g2s(dst, src, part, &sh->full[st]);
-            if (SPLIT) bulk_g2s(dst + kBBytes, src + part, part, &sh->full[st]);
-          }
+          bulk_g2s(dst, src, part, &sh->full[st]);
+          if (SPLIT) bulk_g2s(dst + kBBytes, src + part, part, &sh->full[st]);
         }
       }
     }
@@ -758,7 +699,6 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
 
   fence_before();
   __syncthreads();
-  if (g.cs > 1) cluster_sync();  // no peer still multicasts into this CTA's memory
   if (warp == kAWarps) {
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols)
@@ -854,7 +794,7 @@ cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, in
   e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[2];
+  cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
@@ -862,29 +802,11 @@ cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, in
   cfg.blockDim = dim3(kThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
-  int clusters;
-  if (g.cs > 1) {
-    attr[1].id = cudaLaunchAttributeClusterDimension;
-    attr[1].val.clusterDim.x = g.cs;
-    attr[1].val.clusterDim.y = 1;
-    attr[1].val.clusterDim.z = 1;
-    cfg.numAttrs = 2;
-    // the schedule is static per cluster, so launch only clusters that fit at once
-    cfg.gridDim = dim3(g.cs * (num_sms / g.cs));
-    int fit = 0;
-    e = cudaOccupancyMaxActiveClusters(&fit, (void*)fn, &cfg);
-    if (e != cudaSuccess || fit < 1) {
-      cudaGetLastError();
-      fit = 1;
-    }
-    clusters = grid > 0 ? grid / g.cs : fit;
-    if (clusters > fit) clusters = fit;
-  } else {
-    clusters = grid > 0 ? grid : num_sms;
-  }
-  if (clusters < 1) clusters = 1;
-  if (clusters > g.total_units) clusters = (int)g.total_units;
-  cfg.gridDim = dim3(clusters * g.cs);
+  // persistent: at most one CTA per SM (shared memory and tensor memory allow no more)
+  int ctas = grid > 0 ? std::min(grid, num_sms) : num_sms;
+  if (ctas < 1) ctas = 1;
+  if (ctas > g.total_units) ctas = (int)g.total_units;
+  cfg.gridDim = dim3(ctas);
   return cudaLaunchKernelEx(&cfg, fn, frames, k, g, scaled, out_dtype, status, counter);
 }
 
@@ -892,16 +814,14 @@ cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, in
 
 int tile_nt(int L) { return L >= 128 ? 128 : ((L + 7) / 8) * 8; }
 
-int64_t tensor_split_stride(int V, int Ns, int L) {
-  const int nt = tile_nt(L);
+int64_t tensor_split_stride(int V, int Ns, int L, int nt) {
   const int64_t mtiles = ((int64_t)V * Ns + 127) / 128;
   return mtiles * ((L + nt - 1) / nt) * 128 * nt;
 }
 
-cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
-                                bool scale_from_meta, int num_sms, cudaStream_t st) {
-  const int nt = tile_nt(k.L);
-  const int64_t sstride = tensor_split_stride(k.V, k.Ns, k.L);
+cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int nt,
+                                int out_dtype, bool scale_from_meta, int num_sms, cudaStream_t st) {
+  const int64_t sstride = tensor_split_stride(k.V, k.Ns, k.L, nt);
   const int64_t n4 = sstride / 2;
   if (n4 <= 0 || F <= 0) return cudaSuccess;
   // one wave of resident blocks (8 x 256 threads per SM) over all frames, grid-stride
@@ -913,22 +833,22 @@ cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, i
 }
 
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
-                        int out_dtype, int grid, int cluster, bool use_partial, int num_sms,
+                        int out_dtype, int grid, int nt, int group, bool use_partial, int num_sms,
                         int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st,
                         cudaEvent_t mid) {
+  // N = 2 NT must be a multiple of 16 in 16..256 (kind::f16 with M = 128), and a group
+  // holds at least one chunk
+  if (nt < 8 || nt > kBRowsMax / 2 || nt % 8 != 0 || group < 1) return cudaErrorInvalidValue;
   Geo g;
   const int64_t rows = (int64_t)k.V * k.Ns;
-  g.NT = tile_nt(k.L);
+  g.NT = nt;
   g.ntiles = (k.L + g.NT - 1) / g.NT;
   g.mtiles = (int)((rows + 127) / 128);
-  g.cs = (cluster == 2 || cluster == 4 || cluster == 8) ? cluster : 1;
-  if (g.cs > g.mtiles) g.cs = g.mtiles >= 4 ? 4 : (g.mtiles >= 2 ? 2 : 1);
-  g.mgroups = (g.mtiles + g.cs - 1) / g.cs;
   g.splits = splits;
-  g.upf = g.mgroups * g.ntiles * splits;
-  g.group = group_chunks(tier);
+  g.upf = g.mtiles * g.ntiles * splits;
+  g.group = group;
   g.direct = use_partial ? 0 : 1;
-  g.sstride = tensor_split_stride(k.V, k.Ns, k.L);
+  g.sstride = tensor_split_stride(k.V, k.Ns, k.L, nt);
   g.F = F;
   g.total_units = (int64_t)g.upf * F;
   if (g.total_units <= 0) {

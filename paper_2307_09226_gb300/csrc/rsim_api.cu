@@ -40,7 +40,7 @@ static bool mul_ok(int64_t a, int64_t b, int64_t* out) {
 }
 
 FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_partial, bool tensor,
-                         size_t base) {
+                         int nt, size_t base) {
   FrameLayout fl{};
   const int64_t Pcap = std::max<int64_t>(64, (P + 63) / 64 * 64);
   fl.Pcap = Pcap;
@@ -54,7 +54,7 @@ FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_p
   fl.meta = 0;     // lives in the batch header
   fl.partial = o;
   if (use_partial) {
-    const int64_t per_split = tensor ? tensor_split_stride(V, Ns, L) : (int64_t)V * Ns * L;
+    const int64_t per_split = tensor ? tensor_split_stride(V, Ns, L, nt) : (int64_t)V * Ns * L;
     o = align_up(o + 8 * (size_t)splits * per_split, 256);
   }
   // slow-time operand images: [column tile][chunk][hi, lo][2 NT rows x 128 B]
@@ -62,9 +62,8 @@ FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_p
   fl.bimg = align_up(o, 1024);
   o = fl.bimg;
   if (tensor) {
-    const int nt = tile_nt(L);
     const int ntiles = (L + nt - 1) / nt;
-    o = align_up(o + (size_t)ntiles * fl.bimg_nch * 2 * bimg_part_bytes(L), 256);
+    o = align_up(o + (size_t)ntiles * fl.bimg_nch * 2 * bimg_part_bytes(nt), 256);
   }
   fl.total = o;
   return fl;
@@ -117,40 +116,41 @@ rsim_status check_pixels(const rsim_pixels* px) {
 
 bool tier_ok(int tier) { return tier >= RSIM_TIER_FP32 && tier <= RSIM_TIER_NUFFT; }
 
+// Shape bucket of a plan: the pixel count enters as ceil(log2 P), so frames and requests
+// whose counts lie in one power-of-two range share a tuned plan.
 std::string plan_key(int tier, const Consts& k, int64_t P) {
-  char b[160];
-  snprintf(b, sizeof b, "t%d_V%d_Ns%d_L%d_P%lld", tier, k.V, k.Ns, k.L, (long long)P);
-  return b;
+  int b = 0;
+  while (b < 62 && (int64_t(1) << b) < P) ++b;
+  char s[160];
+  snprintf(s, sizeof s, "t%d_V%d_Ns%d_L%d_b%d", tier, k.V, k.Ns, k.L, b);
+  return s;
 }
-
-// CTAs per cluster of the tensor-core contraction: plan.variant, 0 = the default (1).
-int plan_cluster(const rsim_plan& p) { return p.variant > 0 ? p.variant : 1; }
 
 rsim_plan choose_plan(rsim_ctx* ctx, int tier, const Consts& k, int64_t P) {
   {
     std::lock_guard<std::mutex> g(ctx->plan_mu);
     auto it = ctx->plans.find(plan_key(tier, k, P));
-    if (it != ctx->plans.end()) return it->second;
+    // a cached plan that cannot run this shape (a cache file written for another build)
+    // falls back to the default rule
+    if (it != ctx->plans.end() && plan_problem(tier, k, it->second).empty()) {
+      rsim_plan p = it->second;
+      resolve_tile(tier, k, &p);
+      return p;
+    }
   }
-  rsim_plan p{};
-  p.splits = default_splits(tier, k.V, k.Ns, k.L, P, ctx->num_sms);
-  p.chunk_px = kChunkPx;
-  p.grid = 0;
-  p.variant = 0;
-  p.tuned = 0;
-  return p;
+  return default_plan(tier, k, P, ctx->num_sms);
 }
 
 // Workspace bytes of the per-frame regions of F frames of P_f pixels.
-size_t frames_bytes(const Consts& k, const int64_t* P, int F, int splits, int tier) {
+size_t frames_bytes(const Consts& k, const int64_t* P, int F, const rsim_plan& plan, int tier) {
   int64_t mp = 0;
   for (int f = 0; f < F; ++f) mp = std::max(mp, P[f]);
-  const bool up = uses_partial(tier, mp, splits);
+  const bool up = uses_partial(tier, mp, plan.splits, plan.group_chunks);
   size_t o = align_up(sizeof(FrameIO) * (size_t)F, 256);  // frame table
   o = align_up(o + 16 * (size_t)F, 256);                  // meta
   o = align_up(o + 16 + 4 * (size_t)F, 256);              // unit counter + frame order
   for (int f = 0; f < F; ++f) {
-    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], splits, up, tensor_tier(tier), o);
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P[f], plan.splits, up, tensor_tier(tier), plan.tile_n, o);
     o = fl.total;
   }
   return o;
@@ -161,8 +161,8 @@ int nufft_slots(int F) { return std::max(1, std::min(F, rsim_ctx::kNuStreams)); 
 
 // Workspace bytes for F frames: the per-frame regions, then (NUFFT tier) the grid
 // scratch slots that the frames use in turn.
-size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits, int tier) {
-  size_t o = frames_bytes(k, P, F, splits, tier);
+size_t batch_bytes(const Consts& k, const int64_t* P, int F, const rsim_plan& plan, int tier) {
+  size_t o = frames_bytes(k, P, F, plan, tier);
   if (tier == RSIM_TIER_NUFFT) {
     int64_t mp = 0;
     for (int f = 0; f < F; ++f) mp = std::max(mp, P[f]);
@@ -197,7 +197,7 @@ rsim_status ensure_workspace(rsim_ctx* ctx, size_t bytes, cudaStream_t st) {
 // here; a single frame's entry goes to the first kernel by value (launch_prep), and the
 // meta words and the unit counter are cleared by that kernel too.
 rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pixels* frames,
-                         int F, void* const* cubes, int splits, bool use_partial, bool tensor,
+                         int F, void* const* cubes, int splits, bool use_partial, bool tensor, int nt,
                          cudaStream_t st, std::vector<FrameIO>& host, FrameIO** dev_table,
                          int** counter) {
   host.assign(F, FrameIO{});
@@ -208,7 +208,7 @@ rsim_status stage_frames(rsim_ctx* ctx, char* ws, const Consts& k, const rsim_pi
   o = align_up(o + 16 + 4 * (size_t)F, 256);
   for (int f = 0; f < F; ++f) {
     const rsim_pixels& px = frames[f];
-    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, px.P, splits, use_partial, tensor, o);
+    FrameLayout fl = frame_layout(k.V, k.Ns, k.L, px.P, splits, use_partial, tensor, nt, o);
     o = fl.total;
     FrameIO& io = host[f];
     io.range = px.range;
@@ -254,15 +254,17 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   std::vector<int64_t> Ps(F);
   for (int f = 0; f < F; ++f) Ps[f] = frames[f].P;
   const int splits = plan.splits;
-  if (batch_bytes(k, Ps.data(), F, splits, tier) > ws_bytes)
+  const std::string bad = plan_problem(tier, k, plan);
+  if (!bad.empty()) return fail(RSIM_ERR_INVALID_ARG, bad);
+  if (batch_bytes(k, Ps.data(), F, plan, tier) > ws_bytes)
     return fail(RSIM_ERR_INVALID_ARG, "workspace too small for this request");
   const int64_t mp = max_P(frames, F);
-  const bool use_partial = uses_partial(tier, mp, splits);
+  const bool use_partial = uses_partial(tier, mp, splits, plan.group_chunks);
   std::vector<FrameIO> host;
   FrameIO* table = nullptr;
   int* counter = nullptr;
   rsim_status s = stage_frames(ctx, ws, k, frames, F, cubes, splits, use_partial,
-                               tensor_tier(tier), st, host, &table, &counter);
+                               tensor_tier(tier), plan.tile_n, st, host, &table, &counter);
   if (s != RSIM_OK) return s;
   // stage events when profiling this context's own calls
   // ev: start, after compaction + phases, after the contraction, after the reduction,
@@ -292,7 +294,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   if (prof) cudaEventRecord(ev[1], st);
   if (tier == RSIM_TIER_NUFFT) {
     if (!nufft_supported(k)) return fail(RSIM_ERR_UNSUPPORTED, "the NUFFT tier needs N_s and L in 4..2048");
-    char* scratch = ws + align_up(frames_bytes(k, Ps.data(), F, splits, tier), 256);
+    char* scratch = ws + align_up(frames_bytes(k, Ps.data(), F, plan, tier), 256);
     const size_t slot = align_up(nufft_scratch_bytes(k, mp), 256);
     const int S = nufft_slots(F);
     if (S > 1 && !ctx->nu_ready) {
@@ -340,7 +342,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     if (prof) cudaEventRecord(ev[2], st);
   } else if (tier == RSIM_TIER_FP32) {
     if (prof) cudaEventRecord(ev[4], st);
-    e = launch_direct(k, table, F, splits, out_dtype, st);
+    e = launch_direct(k, table, F, splits, plan.tile_n, out_dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
     if (prof) cudaEventRecord(ev[2], st);
     if (prof) cudaEventRecord(ev[5], st);
@@ -349,15 +351,15 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
     }
   } else {
-    e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, plan_cluster(plan), use_partial,
-                    ctx->num_sms, mp, status, counter, st, prof ? ev[4] : nullptr);
+    e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, plan.tile_n, plan.group_chunks,
+                    use_partial, ctx->num_sms, mp, status, counter, st, prof ? ev[4] : nullptr);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     if (prof) cudaEventRecord(ev[2], st);
     if (prof) cudaEventRecord(ev[5], st);
     if (use_partial) {
       const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
-      e = launch_reduce_tiles(k, table, F, splits, out_dtype, scaled, ctx->num_sms, st);
+      e = launch_reduce_tiles(k, table, F, splits, plan.tile_n, out_dtype, scaled, ctx->num_sms, st);
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
     }
   }
@@ -438,7 +440,7 @@ rsim_status rsim_workspace_size(rsim_ctx* ctx, const rsim_radar_params* params, 
   rsim_status s = check_params(params, &k);
   if (s != RSIM_OK) return s;
   rsim_plan plan = choose_plan(ctx, tier, k, P);
-  *bytes = batch_bytes(k, &P, 1, plan.splits, tier);
+  *bytes = batch_bytes(k, &P, 1, plan, tier);
   return RSIM_OK;
 }
 
@@ -585,7 +587,7 @@ rsim_status rsim_synth_batch(rsim_ctx* ctx, const rsim_radar_params* params,
   rsim_plan plan = choose_plan(ctx, tier, k, maxp);
   std::vector<int64_t> Ps(F);
   for (int f = 0; f < F; ++f) Ps[f] = frames[f].P;
-  const size_t need = batch_bytes(k, Ps.data(), F, plan.splits, tier);
+  const size_t need = batch_bytes(k, Ps.data(), F, plan, tier);
   s = ensure_workspace(ctx, need, st);
   if (s != RSIM_OK) return s;
   return run_frames(ctx, (char*)ctx->ws, ctx->ws_bytes, k, frames, F, cubes, tier, out_dtype, plan,
@@ -604,13 +606,15 @@ rsim_status rsim_valid_indices(rsim_ctx* ctx, const rsim_pixels* pixels, int32_t
   k.Ns = 1;
   k.L = 1;
   int64_t P = pixels->P;
-  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, 1, RSIM_TIER_FP32), st);
+  rsim_plan one{};
+  one.splits = 1;
+  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, one, RSIM_TIER_FP32), st);
   if (s != RSIM_OK) return s;
   std::vector<FrameIO> host;
   FrameIO* table = nullptr;
   int* counter = nullptr;
   void* cubes[1] = {nullptr};
-  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, false, st, host, &table,
+  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, false, 0, st, host, &table,
                    &counter);
   if (s != RSIM_OK) return s;
   // the index list goes straight to the caller's buffer; the count is copied after
@@ -636,13 +640,15 @@ rsim_status rsim_path_phases(rsim_ctx* ctx, const rsim_radar_params* params,
   cudaStream_t st = (cudaStream_t)stream;
   cudaSetDevice(ctx->device);
   int64_t P = pixels->P;
-  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, 1, RSIM_TIER_FP32), st);
+  rsim_plan one{};
+  one.splits = 1;
+  s = ensure_workspace(ctx, batch_bytes(k, &P, 1, one, RSIM_TIER_FP32), st);
   if (s != RSIM_OK) return s;
   std::vector<FrameIO> host;
   FrameIO* table = nullptr;
   int* counter = nullptr;
   void* cubes[1] = {nullptr};
-  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, false, st, host, &table,
+  s = stage_frames(ctx, (char*)ctx->ws, k, pixels, 1, cubes, 1, false, false, 0, st, host, &table,
                    &counter);
   if (s != RSIM_OK) return s;
   host[0].phA = a;
@@ -722,15 +728,17 @@ rsim_status rsim_profile_read(rsim_ctx* ctx, rsim_profile* out) {
 
 rsim_status rsim_set_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_t P,
                           rsim_tier tier, const rsim_plan* plan) {
-  if (!ctx || !plan) return fail(RSIM_ERR_INVALID_ARG, "NULL argument");
+  // the plan is checked before the context is needed, so a bad plan is reported as such
+  if (!plan) return fail(RSIM_ERR_INVALID_ARG, "plan is NULL");
   if (!tier_ok(tier)) return fail(RSIM_ERR_INVALID_ARG, "unknown tier");
-  if (plan->splits < 1 || plan->splits > kMaxSplits || plan->grid < 0)
-    return fail(RSIM_ERR_INVALID_ARG, "plan splits must be in 1..64 and grid >= 0");
   Consts k;
   rsim_status s = check_params(params, &k);
   if (s != RSIM_OK) return s;
+  const std::string bad = plan_problem(tier, k, *plan);
+  if (!bad.empty()) return fail(RSIM_ERR_INVALID_ARG, bad);
+  if (!ctx) return fail(RSIM_ERR_INVALID_ARG, "ctx is NULL");
   rsim_plan p = *plan;
-  p.chunk_px = kChunkPx;
+  resolve_tile(tier, k, &p);
   std::lock_guard<std::mutex> g(ctx->plan_mu);
   ctx->plans[plan_key(tier, k, P)] = p;
   return RSIM_OK;

@@ -46,8 +46,7 @@ rsim_status check_pixels(const rsim_pixels* px);
 bool tier_ok(int tier);
 std::string plan_key(int tier, const Consts& k, int64_t P);
 rsim_plan choose_plan(rsim_ctx* ctx, int tier, const Consts& k, int64_t P);
-int plan_cluster(const rsim_plan& p);
-size_t batch_bytes(const Consts& k, const int64_t* P, int F, int splits, int tier);
+size_t batch_bytes(const Consts& k, const int64_t* P, int F, const rsim_plan& plan, int tier);
 rsim_status ensure_workspace(rsim_ctx* ctx, size_t bytes, cudaStream_t st);
 rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k,
                        const rsim_pixels* frames, int F, void* const* cubes, int tier,

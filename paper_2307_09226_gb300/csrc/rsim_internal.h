@@ -62,15 +62,15 @@ struct FrameLayout {
   size_t idx, phA, phC, phB, sig, blk, meta, partial, bimg, total;
   int64_t Pcap, bimg_nch;
 };
+// nt: the plan's column tile of the tensor tiers (ignored otherwise).
 FrameLayout frame_layout(int V, int Ns, int L, int64_t P, int splits, bool use_partial, bool tensor,
-                         size_t base);
-// Columns of l per tensor-core column tile, and the bytes of one 16-bit part of one
-// chunk's slow-time operand image (2 NT rows of 128 B).
+                         int nt, size_t base);
+// Default columns of l per tensor-core column tile: min(128, L rounded up to 8).
 int tile_nt(int L);
-// Complex elements of one split's partial sums on the tensor tiers.  They are stored
-// by accumulator tile, [row tile][column tile][column pair][128 rows][2 columns], so
-// that a warp's 32 accumulator rows drain into 512 contiguous bytes.
-int64_t tensor_split_stride(int V, int Ns, int L);
+// Complex elements of one split's partial sums on the tensor tiers with column tile nt.
+// They are stored by accumulator tile, [row tile][column tile][column pair][128 rows][2
+// columns], so that a warp's 32 accumulator rows drain into 512 contiguous bytes.
+int64_t tensor_split_stride(int V, int Ns, int L, int nt);
 
 // Tensor-core tiers (the tcgen05 contraction and its operand images).
 inline bool tensor_tier(int tier) {
@@ -172,7 +172,8 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   c = (t - s) - y;
   s = t;
 }
-inline size_t bimg_part_bytes(int L) { return (size_t)2 * tile_nt(L) * 128; }
+// Bytes of one 16-bit part of one chunk's slow-time operand image (2 NT rows of 128 B).
+inline size_t bimg_part_bytes(int nt) { return (size_t)2 * nt * 128; }
 
 // Launches (all asynchronous on `st`).  `frames` is a device array of F FrameIO.
 // Compaction and phases.  `one` (F == 1 only, else NULL): the frame's entry, which the
@@ -180,18 +181,19 @@ inline size_t bimg_part_bytes(int L) { return (size_t)2 * tile_nt(L) * 128; }
 // frame's meta words and, when `counter` is given, the contraction's work-unit counter.
 cudaError_t launch_prep(const Consts& k, FrameIO* frames, const FrameIO* one, int F, int64_t maxP,
                         int dtype, bool write_idx_only, unsigned* status, int* counter, cudaStream_t st);
-cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits,
+// tile_n: n values per CTA tile (64 or 128).
+cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits, int tile_n,
                           int out_dtype, cudaStream_t st);
 cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
                           float scale_from_meta, cudaStream_t st);
 // The same reduction over the tensor tiers' tiled partial sums.
-cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
-                                bool scale_from_meta, int num_sms, cudaStream_t st);
-// cluster: CTAs per thread-block cluster that share the slow-time operand by
-// multicast (1, 2, 4 or 8).  mid: an event recorded between the operand builder and
-// the contraction kernel (profiling), or NULL.
+cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int nt,
+                                int out_dtype, bool scale_from_meta, int num_sms, cudaStream_t st);
+// nt: column tile (l values, multiple of 8 in 8..128); group: chunks per accumulation
+// group.  mid: an event recorded between the operand builder and the contraction
+// kernel (profiling), or NULL.
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
-                        int out_dtype, int grid, int cluster, bool use_partial, int num_sms,
+                        int out_dtype, int grid, int nt, int group, bool use_partial, int num_sms,
                         int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st,
                         cudaEvent_t mid = nullptr);
 
@@ -199,13 +201,24 @@ cudaError_t launch_range_doppler(const float2* const* cubes_dev, float2* tmp, fl
                                  int V, int Ns, int L, int skip_static, double v_per_bin, float* v_est,
                                  int32_t* peak, cudaStream_t st);
 
-// Plan rule shared by single-frame and batch paths (depends on the shape only).
-int default_splits(int tier, int V, int Ns, int L, int64_t P, int num_sms);
-int units_per_split(int tier, int V, int Ns, int L);
-// Chunks accumulated in one tensor-memory accumulator before it is drained into an
-// FP32 running sum (the tensor-core accumulator rounds toward zero; see k_umma.cu).
+// Plan rules shared by single-frame and batch paths (they depend on the shape only).
+// tile_n: the plan's tile (tensor tiers: column tile NT; FP32: n per CTA tile).
+int default_splits(int tier, int V, int Ns, int L, int tile_n, int64_t P, int num_sms);
+int units_per_split(int tier, int V, int Ns, int L, int tile_n);
+// Default and largest chunks accumulated in one tensor-memory accumulator before it is
+// drained into an FP32 running sum (the tensor-core accumulator rounds toward zero, so
+// the length bounds the error; see k_umma.cu).
 int group_chunks(int tier);
+int group_chunks_max(int tier);
+// Default n tile of the FP32 direct sum.
+constexpr int kDirectTileN = 128;
 // Whether a frame of P pixels goes through the split-partial buffer + reduction.
-bool uses_partial(int tier, int64_t P, int splits);
+bool uses_partial(int tier, int64_t P, int splits, int group);
+
+// Plans: the default for a shape, defaults filled into zero tile fields, and validity
+// (an empty string when the plan can run this shape at this tier's accuracy).
+rsim_plan default_plan(int tier, const Consts& k, int64_t P, int num_sms);
+void resolve_tile(int tier, const Consts& k, rsim_plan* p);
+std::string plan_problem(int tier, const Consts& k, const rsim_plan& p);
 
 }  // namespace rsim

@@ -1,9 +1,12 @@
 // Serving loop: continuous batching of cube-synthesis requests.
 //
 // Each slot owns two CUDA streams, of the highest and the lowest priority, and a status
-// word.  A scheduler thread admits the head of the FIFO queue as soon as a slot is free
-// and the request's workspace fits in the part of the HBM budget that running requests
-// have not reserved.  A request whose estimated device time is short runs on the
+// word.  A scheduler thread admits a queued request as soon as a slot is free and the
+// request's workspace fits in the part of the HBM budget that running requests have not
+// reserved: the oldest that fits (first fit), or the one with the least estimated device
+// time among those that fit (shortest first).  A request can be passed over only until
+// it has waited the age limit; after that it is next, whether or not it fits yet, so no
+// request starves.  A request whose estimated device time is short runs on the
 // high-priority stream: when long requests' kernels hold the SMs, the block scheduler
 // starts its blocks as soon as any resources free up instead of after the long kernels'
 // remaining blocks.  (Measured on the mixed serving workload: p50 and p99 both lower than
@@ -44,7 +47,8 @@ struct Req {
   size_t bytes = 0;
   int state = kQueued;
   rsim_status result = RSIM_OK;
-  Clock::time_point t_submit, t_done;
+  Clock::time_point t_submit, t_admit, t_done;
+  double est_ms = 0.0;  // estimated device time: path-samples at the tier's nominal rate
   int slot = -1;
   int prio = 0;  // index into the slot's streams: 0 high priority, 1 low
   void* ws = nullptr;
@@ -79,7 +83,8 @@ struct rsim_server {
   size_t reserved = 0;
   // statistics
   rsim_server_stats stats{};
-  std::vector<double> lat_ms;
+  std::vector<double> lat_ms, queue_ms;
+  std::chrono::milliseconds age_limit{100};  // overtaking allowed until a request waited this long
   bool have_first = false;
   rsim::Clock::time_point t_first, t_last;
   int in_flight = 0;
@@ -134,6 +139,7 @@ void retire(rsim_server* s, int si) {
     if (r.result == RSIM_OK) {
       s->stats.completed++;
       s->lat_ms.push_back(ms);
+      s->queue_ms.push_back(std::chrono::duration<double, std::milli>(r.t_admit - r.t_submit).count());
       s->stats.path_samples += (double)(*sl.pv_host) * r.k.V * r.k.Ns * r.k.L;
     } else {
       s->stats.failed++;
@@ -145,7 +151,25 @@ void retire(rsim_server* s, int si) {
   s->in_flight--;
 }
 
-// Try to start the head request on a free slot.  Called with the lock held.
+// Position in the queue of the request to admit next, or -1 when none may start now.
+// The queue is in submission order, so its head is the oldest request: once the head has
+// waited the age limit (or the limit is negative: strict FIFO) only the head may start.
+long pick_next(rsim_server* s, Clock::time_point now) {
+  const size_t budget = s->opts.hbm_budget_bytes;
+  auto fits = [&](const Req& r) { return !budget || s->reserved + r.bytes <= budget; };
+  const Req& head = s->reqs[s->queue.front()];
+  if (s->opts.age_limit_ms < 0 || now - head.t_submit >= s->age_limit) return fits(head) ? 0 : -1;
+  long best = -1;
+  for (size_t i = 0; i < s->queue.size(); ++i) {
+    const Req& r = s->reqs[s->queue[i]];
+    if (!fits(r)) continue;
+    if (s->opts.policy == RSIM_SERVE_FIRST_FIT) return (long)i;
+    if (best < 0 || r.est_ms < s->reqs[s->queue[best]].est_ms) best = (long)i;
+  }
+  return best;
+}
+
+// Try to start one queued request on a free slot.  Called with the lock held.
 bool admit_one(rsim_server* s) {
   if (s->queue.empty()) return false;
   int free_slot = -1;
@@ -155,9 +179,13 @@ bool admit_one(rsim_server* s) {
       break;
     }
   if (free_slot < 0) return false;
-  Req& r = s->reqs[s->queue.front()];
-  if (s->opts.hbm_budget_bytes && s->reserved + r.bytes > s->opts.hbm_budget_bytes) return false;
-  s->queue.pop_front();
+  const Clock::time_point now = Clock::now();
+  const long qi = pick_next(s, now);
+  if (qi < 0) return false;
+  Req& r = s->reqs[s->queue[qi]];
+  if (qi > 0) s->stats.overtakes++;
+  s->queue.erase(s->queue.begin() + qi);
+  r.t_admit = now;
   Slot& sl = s->slots[free_slot];
   cudaStream_t rs = sl.st[r.prio];
   cudaError_t e = cudaMallocAsync(&r.ws, r.bytes, rs);
@@ -243,10 +271,13 @@ rsim_status rsim_server_create(rsim_ctx* ctx, const rsim_server_opts* opts, rsim
   if (!ctx || !opts || !out) return fail(RSIM_ERR_INVALID_ARG, "NULL argument");
   if (opts->slots < 1 || opts->slots > 64) return fail(RSIM_ERR_INVALID_ARG, "slots must be in 1..64");
   if (opts->max_queue < 1) return fail(RSIM_ERR_INVALID_ARG, "max_queue must be >= 1");
+  if (opts->policy != RSIM_SERVE_FIRST_FIT && opts->policy != RSIM_SERVE_SHORTEST_FIRST)
+    return fail(RSIM_ERR_INVALID_ARG, "unknown admission policy");
   cudaSetDevice(ctx->device);
   rsim_server* s = new rsim_server();
   s->ctx = ctx;
   s->opts = *opts;
+  if (opts->age_limit_ms > 0) s->age_limit = std::chrono::milliseconds(opts->age_limit_ms);
   s->slots.resize(opts->slots);
   for (int i = 0; i < opts->slots; ++i) {
     Slot& sl = s->slots[i];
@@ -287,12 +318,12 @@ rsim_status rsim_server_submit(rsim_server* s, const rsim_request* req, uint64_t
     return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tiers need an sm_103 device");
   r.plan = choose_plan(s->ctx, req->tier, r.k, req->pixels.P);
   int64_t P = req->pixels.P;
-  r.bytes = batch_bytes(r.k, &P, 1, r.plan.splits, req->tier);
+  r.bytes = batch_bytes(r.k, &P, 1, r.plan, req->tier);
   // estimated device time from the path-samples at the tier's nominal rate (CUDA cores
   // about 6e12/s, tensor cores and the NUFFT about 6e13/s): high priority under 2 ms
   const double work = (double)req->pixels.P * r.k.V * r.k.Ns * r.k.L;
-  const double est_ms = work / (req->tier == RSIM_TIER_FP32 ? 6e12 : 6e13) * 1e3;
-  r.prio = est_ms < 2.0 ? 0 : 1;
+  r.est_ms = work / (req->tier == RSIM_TIER_FP32 ? 6e12 : 6e13) * 1e3;
+  r.prio = r.est_ms < 2.0 ? 0 : 1;
   std::lock_guard<std::mutex> g(s->mu);
   if (s->opts.hbm_budget_bytes && r.bytes > s->opts.hbm_budget_bytes)
     return fail(RSIM_ERR_BUDGET, "request workspace exceeds the server HBM budget");
@@ -360,6 +391,8 @@ rsim_status rsim_server_stats_get(rsim_server* s, rsim_server_stats* out) {
   }
   out->mean_ms = s->lat_ms.empty() ? 0 : sum / s->lat_ms.size();
   out->max_ms = mx;
+  out->p99_queue_ms = percentile(s->queue_ms, 0.99);
+  out->max_queue_ms = s->queue_ms.empty() ? 0.0 : *std::max_element(s->queue_ms.begin(), s->queue_ms.end());
   out->busy_s = s->have_first ? std::chrono::duration<double>(s->t_last - s->t_first).count() : 0.0;
   return RSIM_OK;
 }
@@ -371,6 +404,7 @@ rsim_status rsim_server_stats_reset(rsim_server* s) {
   s->stats.peak_reserved_bytes = s->reserved;
   s->stats.peak_in_flight = s->in_flight;
   s->lat_ms.clear();
+  s->queue_ms.clear();
   s->have_first = false;
   return RSIM_OK;
 }

@@ -75,13 +75,14 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   // the plan is the library's default rule for this shape (what rsim_synth uses
   // without a tuned plan); the scratch layout mirrors the context workspace
   const int64_t P = pixels->P;
-  const int splits = default_splits(tier, k.V, k.Ns, k.L, P, sms);
-  const bool use_partial = uses_partial(tier, P, splits);
+  const rsim_plan plan = default_plan(tier, k, P, sms);
+  const int splits = plan.splits;
+  const bool use_partial = uses_partial(tier, P, splits, plan.group_chunks);
   size_t o = 0;
   const size_t off_table = o;   o = up256(o + sizeof(FrameIO));
   const size_t off_meta = o;    o = up256(o + 16);
   const size_t off_counter = o; o = up256(o + 16 + 4);
-  FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P, splits, use_partial, tensor_tier(tier), o);
+  FrameLayout fl = frame_layout(k.V, k.Ns, k.L, P, splits, use_partial, tensor_tier(tier), plan.tile_n, o);
   o = fl.total;
   const size_t off_status = o;  o = up256(o + 4);
   if (o > kStaticWsBytes)
@@ -127,16 +128,16 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   e = launch_prep(k, table, &io, 1, P, pixels->dtype, false, status, counter, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (tier == RSIM_TIER_FP32) {
-    e = launch_direct(k, table, 1, splits, out_dtype, st);
+    e = launch_direct(k, table, 1, splits, plan.tile_n, out_dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
     if (use_partial) e = launch_reduce(k, table, 1, splits, out_dtype, 0.f, st);
   } else {
-    e = launch_umma(k, table, 1, splits, tier, out_dtype, 0, 1, use_partial, sms, P, status,
-                    counter, st);
+    e = launch_umma(k, table, 1, splits, tier, out_dtype, 0, plan.tile_n, plan.group_chunks, use_partial, sms,
+                    P, status, counter, st);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
-    if (use_partial) e = launch_reduce_tiles(k, table, 1, splits, out_dtype, scaled, sms, st);
+    if (use_partial) e = launch_reduce_tiles(k, table, 1, splits, plan.tile_n, out_dtype, scaled, sms, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "split reduction");
   return RSIM_OK;

@@ -1,11 +1,18 @@
-// Autotuner: times candidate launch plans for a shape and caches the fastest.
+// Autotuner: times candidate launch plans for a shape bucket and caches the fastest.
 //
-// A plan is (pixel splits, CTAs of the persistent contraction).  The key is the
-// shape only (tier, V, N_s, L, P), never the load or the data, so the same frame
-// always runs the same kernels with the same reduction order.  Timings use CUDA
-// events on the caller's stream over synthetic full-valid pixels drawn on the device
-// by a counter-based hash.  Results live in the context and, when RSIM_TUNE_CACHE
-// names a file, in a small JSON object {"key": [splits, grid, variant], ...}.
+// A plan holds the tile shapes and the work split of one shape bucket (tier, V, N_s, L,
+// ceil(log2 P)): the column tile NT and the accumulation-group length of the
+// tensor-core contraction, or the n tile of the FP32 direct sum, plus the pixel split
+// count and the persistent grid.  The search is coordinate-wise, so its cost stays a
+// dozen or two timed runs: first the tile (each with its own default split count), then
+// splits x grid with the best tile, then the group length.  Every candidate keeps the
+// accuracy rules (at most 8192 pixels per FP32 split, group lengths within the tier's
+// cap), so a tuned plan meets the same error bar as the default.  The key is the shape
+// only, never the load or the data, so the same frame always runs the same kernels with
+// the same reduction order.  Timings use CUDA events on the caller's stream over
+// synthetic full-valid pixels drawn on the device by a counter-based hash.  Results
+// live in the context and, when RSIM_TUNE_CACHE names a file, in a small JSON object
+// {"key": [splits, grid, tile_n, group_chunks], ...}.
 #include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
@@ -67,13 +74,15 @@ void parse_cache(const std::string& text, std::map<std::string, rsim_plan>& out)
     std::string key = text.substr(a + 1, b - a - 1);
     size_t lb = text.find('[', b), rb = text.find(']', b);
     if (lb == std::string::npos || rb == std::string::npos) break;
-    int s = 0, g = 0, v = 0;
-    if (sscanf(text.c_str() + lb + 1, "%d , %d , %d", &s, &g, &v) == 3 && s >= 1 && s <= kMaxSplits &&
-        g >= 0) {
+    int s = 0, g = 0, t = 0, gc = 0;
+    // entries are checked against the shape again when used (choose_plan)
+    if (sscanf(text.c_str() + lb + 1, "%d , %d , %d , %d", &s, &g, &t, &gc) == 4 && s >= 1 && s <= kMaxSplits &&
+        g >= 0 && t >= 0 && gc >= 0) {
       rsim_plan p{};
       p.splits = s;
       p.grid = g;
-      p.variant = v;
+      p.tile_n = t;
+      p.group_chunks = gc;
       p.chunk_px = kChunkPx;
       p.tuned = 1;
       out[key] = p;
@@ -92,8 +101,8 @@ void save_plan_cache(rsim_ctx* ctx) {
   bool first = true;
   for (auto& kv : ctx->plans) {
     if (!kv.second.tuned) continue;
-    fprintf(f, "%s  \"%s\": [%d, %d, %d]", first ? "" : ",\n", kv.first.c_str(), kv.second.splits,
-            kv.second.grid, kv.second.variant);
+    fprintf(f, "%s  \"%s\": [%d, %d, %d, %d]", first ? "" : ",\n", kv.first.c_str(), kv.second.splits,
+            kv.second.grid, kv.second.tile_n, kv.second.group_chunks);
     first = false;
   }
   fprintf(f, "\n}\n");
@@ -132,17 +141,6 @@ extern "C" rsim_status rsim_autotune(rsim_ctx* ctx, const rsim_radar_params* par
   cudaSetDevice(ctx->device);
   cudaStream_t st = (cudaStream_t)stream;
 
-  // candidate splits around the default rule, candidate grids for the persistent kernel
-  const int s0 = default_splits(tier, k.V, k.Ns, k.L, P, ctx->num_sms);
-  std::vector<int> cand_s;
-  for (int m : {1, 2, 3, 4, 6, 8}) {
-    int a = std::max(1, s0 * m / 4);
-    a = std::min(a, kMaxSplits);
-    if (std::find(cand_s.begin(), cand_s.end(), a) == cand_s.end()) cand_s.push_back(a);
-  }
-  std::vector<int> cand_g = {0};
-  if (tensor_tier(tier)) cand_g = {ctx->num_sms, ctx->num_sms / 2};
-
   // synthetic pixels and an output buffer
   float* px = nullptr;
   void* cube = nullptr;
@@ -161,45 +159,96 @@ extern "C" rsim_status rsim_autotune(rsim_ctx* ctx, const rsim_radar_params* par
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  float best = 1e30f;
-  rsim_plan best_plan{};
   rsim_status err = RSIM_OK;
-  for (int sp : cand_s) {
-    for (int g : cand_g) {
-      rsim_plan p{};
-      p.splits = sp;
-      p.grid = g;
-      p.chunk_px = kChunkPx;
-      p.tuned = 1;
-      int64_t PP = P;
-      s = ensure_workspace(ctx, batch_bytes(k, &PP, 1, sp, tier), st);
-      if (s != RSIM_OK) {
-        err = s;
-        break;
-      }
-      void* cubes[1] = {cube};
-      float tbest = 1e30f;
-      for (int rep = 0; rep < 4 && s == RSIM_OK; ++rep) {
-        cudaEventRecord(e0, st);
-        s = run_frames(ctx, (char*)ctx->ws, ctx->ws_bytes, k, &pix, 1, cubes, tier, RSIM_C64, p,
-                       ctx->status_dev, st);
-        cudaEventRecord(e1, st);
-        cudaEventSynchronize(e1);
-        float ms = 0;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (rep > 0) tbest = std::min(tbest, ms);  // first run is a warm-up
-      }
-      if (s != RSIM_OK) {
-        err = s;
-        break;
-      }
-      if (tbest < best) {
-        best = tbest;
-        best_plan = p;
+  // time one plan: a warm-up run, then the best of two (1e30 if it cannot run)
+  auto time_plan = [&](const rsim_plan& p) -> float {
+    if (err != RSIM_OK || !plan_problem(tier, k, p).empty()) return 1e30f;
+    int64_t PP = P;
+    rsim_status s2 = ensure_workspace(ctx, batch_bytes(k, &PP, 1, p, tier), st);
+    if (s2 != RSIM_OK) {
+      err = s2;
+      return 1e30f;
+    }
+    void* cubes[1] = {cube};
+    float tbest = 1e30f;
+    for (int rep = 0; rep < 3 && s2 == RSIM_OK; ++rep) {
+      cudaEventRecord(e0, st);
+      s2 = run_frames(ctx, (char*)ctx->ws, ctx->ws_bytes, k, &pix, 1, cubes, tier, RSIM_C64, p, ctx->status_dev,
+                      st);
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0) tbest = std::min(tbest, ms);
+    }
+    if (s2 != RSIM_OK) err = s2;
+    return tbest;
+  };
+  const bool tensor = tensor_tier(tier);
+  // FP32: at most 8192 pixels per split (the accuracy rule of the default plan)
+  const int smin = tier == RSIM_TIER_FP32 ? (int)std::min<int64_t>(std::max<int64_t>((P + 8191) / 8192, 1), kMaxSplits)
+                                          : 1;
+
+  // 1. the tile, each candidate with its own default split count
+  rsim_plan best = default_plan(tier, k, P, ctx->num_sms);
+  std::vector<int> tiles = {best.tile_n};
+  if (tier == RSIM_TIER_FP32) tiles.push_back(64);
+  if (tensor && best.tile_n > 64) tiles.push_back(64);
+  float tb = 1e30f;
+  for (int t : tiles) {
+    rsim_plan p = best;
+    p.tile_n = t;
+    p.splits = default_splits(tier, k.V, k.Ns, k.L, t, P, ctx->num_sms);
+    const float ms = time_plan(p);
+    if (ms < tb) {
+      tb = ms;
+      best = p;
+    }
+  }
+  // 2. splits around the tile's default rule, and the persistent grid (tensor tiers)
+  {
+    const int s0 = best.splits;
+    std::vector<int> cand_s;
+    for (int m : {2, 3, 4, 6, 8}) {
+      int a = std::min(std::max(smin, s0 * m / 4), kMaxSplits);
+      if (std::find(cand_s.begin(), cand_s.end(), a) == cand_s.end()) cand_s.push_back(a);
+    }
+    std::vector<int> cand_g = {0};
+    if (tensor) cand_g.push_back(ctx->num_sms / 2);
+    const rsim_plan base = best;
+    for (int sp : cand_s) {
+      for (int g : cand_g) {
+        if (sp == base.splits && g == base.grid) continue;
+        rsim_plan p = base;
+        p.splits = sp;
+        p.grid = g;
+        const float ms = time_plan(p);
+        if (ms < tb) {
+          tb = ms;
+          best = p;
+        }
       }
     }
-    if (err != RSIM_OK) break;
   }
+  // 3. the accumulation-group length (tensor tiers), never above the tier's cap
+  if (tensor) {
+    const int gmax = group_chunks_max(tier);
+    std::vector<int> cand = (tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16)
+                                ? std::vector<int>{32, gmax}
+                                : std::vector<int>{192, gmax};
+    const rsim_plan base = best;
+    for (int gc : cand) {
+      if (gc == base.group_chunks || gc > gmax) continue;
+      rsim_plan p = base;
+      p.group_chunks = gc;
+      const float ms = time_plan(p);
+      if (ms < tb) {
+        tb = ms;
+        best = p;
+      }
+    }
+  }
+  best.tuned = 1;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaStreamSynchronize(st);
@@ -210,9 +259,9 @@ extern "C" rsim_status rsim_autotune(rsim_ctx* ctx, const rsim_radar_params* par
   if (e != cudaSuccess) return cuda_fail(e, "autotune");
   {
     std::lock_guard<std::mutex> g(ctx->plan_mu);
-    ctx->plans[plan_key(tier, k, P)] = best_plan;
+    ctx->plans[plan_key(tier, k, P)] = best;
     save_plan_cache(ctx);
   }
-  *chosen = best_plan;
+  *chosen = best;
   return RSIM_OK;
 }
