@@ -309,7 +309,7 @@ def run_gpu(args):
     for t in tiers:
         try:
             # every tier runs (and is checked with) the tuned plan of the frame's shape bucket
-            _abi.rsim_autotune(ctx.h, radar, frame.pixels.P, _abi.TIERS[t])
+            ensure_tuned(ctx, radar, frame.pixels.P, t)
             cube = ctx.synth(radar, px, t)
             st = ctx.sync_status()
         except _abi.RsimError as e:
@@ -476,6 +476,15 @@ def _load_traffic(tier):
     return None
 
 
+def ensure_tuned(ctx, radar, P, tier):
+    """Tune the plan of (radar, P, tier)'s shape bucket unless a tuned plan is already
+    cached (RSIM_TUNE_CACHE, which main() points at a file in the temp folder by default,
+    so a second run of the same command, e.g. under a profiler, reuses the plans)."""
+    from paper_2307_09226_gb300 import _abi
+    if not _abi.rsim_get_plan(ctx.h, radar, P, _abi.TIERS[tier]).tuned:
+        _abi.rsim_autotune(ctx.h, radar, P, _abi.TIERS[tier])
+
+
 def run_batch(ctx, tier, steps, warmup):
     """Config 4: 64 walking-pedestrian frames (uneven valid-pixel counts) in one
     rsim_synth_batch call per step; inputs resident, L2 flushed between steps."""
@@ -494,7 +503,7 @@ def run_batch(ctx, tier, steps, warmup):
     P = max(f.pixels.P for f in frames)
     plan = None
     if tier in _abi.TIERS and tier != "nufft":
-        _abi.rsim_autotune(ctx.h, radar, P, _abi.TIERS[tier])
+        ensure_tuned(ctx, radar, P, tier)
         plan = _abi.rsim_get_plan(ctx.h, radar, P, _abi.TIERS[tier]).as_dict()
     for _ in range(warmup):
         ctx.synth_batch(radar, pxs, tier, cubes=cubes)
@@ -679,7 +688,7 @@ def run_raycast(ctx, tier, steps=10, warmup=3):
                         "speed_m_s": round(scenes[0][1]["speed"], 3)}}
 
 
-def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5, tune_budget_s=45.0):
+def run_serving(ctx, tune_budget_s=45.0):
     """Config 5: Poisson stream of mixed requests (M 2-4, N 4-12, Ns 128-512, L 64-256,
     64^2..512^2 pixels, FP32 and split-BF16 tiers) into the continuous-batching server:
     n_warmup requests, a new tally, then n_requests measured; latency is submit ->
@@ -691,6 +700,9 @@ def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5, t
     import numpy as np
     import torch
     from paper_2307_09226_gb300 import _abi, device, synth
+    cfg = synth.load_config(5)
+    n_requests, n_warmup, pool = cfg["requests"], cfg["warmup_requests"], cfg["distinct_frames"]
+    slots, seed, age_ms = cfg["slots"], cfg["seed"], cfg["age_limit_ms"]
     reqs = synth.serving_requests(pool, seed=seed)
     frames = [synth.request_frame(r) for r in reqs]
     pxs = [device.upload(f) for f in frames]
@@ -709,7 +721,7 @@ def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5, t
     for key, (work, rd, P, tier) in sorted(keys.items(), key=lambda kv: kv[1][0]):
         if time.perf_counter() - t_tune > tune_budget_s:
             break
-        _abi.rsim_autotune(ctx.h, rd, P, _abi.TIERS[tier])
+        ensure_tuned(ctx, rd, P, tier)
         tuned.add(key)
     tune_s = time.perf_counter() - t_tune
     on_tuned = sum(1 for r, f in zip(reqs, frames)
@@ -725,7 +737,7 @@ def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5, t
 
     def run(load, policy):
         rate = load / alone_s
-        srv = _abi.rsim_server_create(ctx.h, slots=slots, policy=policy)
+        srv = _abi.rsim_server_create(ctx.h, slots=slots, policy=policy, age_limit_ms=age_ms)
         bad = 0
 
         def stream(n, first):
@@ -759,10 +771,11 @@ def run_serving(ctx, n_requests=2000, n_warmup=100, pool=120, slots=4, seed=5, t
                 "value": st.path_samples / max(st.busy_s, 1e-9) / 1e9, "unit": "Gpath-samples/s",
                 "failed": int(st.failed) + bad, "peak_in_flight": int(st.peak_in_flight)}
 
-    runs = [run(0.7, "first_fit"), run(0.5, "first_fit"), run(0.7, "shortest_first")]
+    loads = cfg["offered_loads"]
+    runs = [run(x, "first_fit") for x in loads] + [run(loads[0], "shortest_first")]
     head = dict(runs[0])
-    head.update({"workload": "poisson-mix-M2..4-N4..12-Ns128..512-L64..256-P4k..262k",
-                 "warmup_requests": n_warmup, "distinct_frames": pool, "slots": slots, "age_limit_ms": 100,
+    head.update({"workload": cfg["workload"],
+                 "warmup_requests": n_warmup, "distinct_frames": pool, "slots": slots, "age_limit_ms": age_ms,
                  "alone_mean_ms": round(alone_s * 1e3, 3),
                  "tuning": {"buckets": len(keys), "tuned": len(tuned), "requests_on_tuned_plans": on_tuned,
                             "pool": pool, "seconds": round(tune_s, 1)},
@@ -782,6 +795,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
+    import tempfile
+    os.environ.setdefault("RSIM_TUNE_CACHE", os.path.join(tempfile.gettempdir(), "rsim_tune_cache.json"))
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -208,14 +208,22 @@ rsim_status rsim_synth_batch(rsim_ctx* ctx, const rsim_radar_params* params,
  *
  * device_status: optional DEVICE pointer to a uint32 that the kernels OR their
  * status bits into (1: a valid pixel had a non-finite field or R <= 0; 2: a
- * device-side wait ran out of time); the caller clears it.  With NULL, a word inside
- * the static array is used and cleared on every call.
+ * device-side wait ran out of time); the caller clears it.  With NULL, the kernels
+ * report into a word inside the static array that the next call clears, and nothing
+ * reads it: a non-finite pixel or a wait that ran out then leaves a wrong cube while
+ * the call still returns RSIM_OK.  Callers that need to know must pass a word.
  *
  * The first call on a device, with that device current, looks up the array's device
- * address (cudaGetSymbolAddress) and caches it; make that first call before any
- * stream capture.  All calls on a device share the one array and it keeps the last
- * call's contents (the call clears what must start at zero), so calls whose work
- * overlaps on the GPU (other streams, other host threads) race: serialise them.
+ * address (cudaGetSymbolAddress) and caches it per device for the life of the
+ * process; make that first call before any stream capture.  With CUDA's lazy module
+ * loading (the default) the array is committed in device memory when the library's
+ * kernels are first loaded on that device, typically by this first call, so a process
+ * with a fixed memory budget should make one warm-up call at start-up.  A device reset
+ * (cudaDeviceReset, or a reset of the primary context) may move the array: the cached
+ * address is then stale and this entry point must not be used again in that process.
+ * All calls on a device share the one array and it keeps the last call's contents (the
+ * call clears what must start at zero), so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race: serialise them.
  * Asynchronous on `stream`.  Errors: INVALID_ARG, OVERFLOW, BUDGET, UNSUPPORTED, CUDA. */
 rsim_status rsim_synth_static(const rsim_radar_params* params, const rsim_pixels* pixels,
                               rsim_tier tier, void* cube, int32_t out_dtype, uint32_t* device_status,

@@ -253,6 +253,11 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
                        int out_dtype, const rsim_plan& plan, unsigned* status, cudaStream_t st) {
   std::vector<int64_t> Ps(F);
   for (int f = 0; f < F; ++f) Ps[f] = frames[f].P;
+  static const char* const kTierName[] = {"fp32", "bf16", "split_bf16", "split_fp16", "fp16", "nufft"};
+  char what[160];
+  snprintf(what, sizeof what, "synth %s F=%d V=%d Ns=%d L=%d P=%lld splits=%d tile=%d", kTierName[tier], F, k.V,
+           k.Ns, k.L, (long long)max_P(frames, F), plan.splits, plan.tile_n);
+  NvtxRange call_range(what);
   const int splits = plan.splits;
   const std::string bad = plan_problem(tier, k, plan);
   if (!bad.empty()) return fail(RSIM_ERR_INVALID_ARG, bad);
@@ -288,8 +293,11 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
                               : tensor ? 1 + (mp > 0 ? 1 : 0) + (F > 1 ? 1 : 0) : 1) + (use_partial ? 1 : 0);
     cudaEventRecord(ev[0], st);
   }
-  cudaError_t e = launch_prep(k, table, F == 1 ? host.data() : nullptr, F, mp, frames[0].dtype, false, status,
-                              counter, st);
+  cudaError_t e;
+  {
+    NvtxRange r("compaction + FP64 phases");
+    e = launch_prep(k, table, F == 1 ? host.data() : nullptr, F, mp, frames[0].dtype, false, status, counter, st);
+  }
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (prof) cudaEventRecord(ev[1], st);
   if (tier == RSIM_TIER_NUFFT) {
@@ -326,6 +334,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
       if (e != cudaSuccess) return cuda_fail(e, "fork of the NUFFT streams");
     }
     cudaError_t le = cudaSuccess;
+    NvtxRange r("NUFFT: binning, spreading, FFTs");
     for (int f = 0; f < F && le == cudaSuccess; ++f) {
       // the first frame's spreading kernel is bracketed by ev[4] and ev[5]
       cudaStream_t fs = S > 1 ? ctx->nu_st[f % S] : st;
@@ -342,6 +351,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     if (prof) cudaEventRecord(ev[2], st);
   } else if (tier == RSIM_TIER_FP32) {
     if (prof) cudaEventRecord(ev[4], st);
+    NvtxRange r("FP32 direct sum + split reduction");
     e = launch_direct(k, table, F, splits, plan.tile_n, out_dtype, st);
     if (e != cudaSuccess) return cuda_fail(e, "direct-sum kernel");
     if (prof) cudaEventRecord(ev[2], st);
@@ -351,6 +361,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
       if (e != cudaSuccess) return cuda_fail(e, "split reduction");
     }
   } else {
+    NvtxRange r("operand images + tcgen05 contraction + split reduction");
     e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, plan.tile_n, plan.group_chunks,
                     use_partial, ctx->num_sms, mp, status, counter, st, prof ? ev[4] : nullptr);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");

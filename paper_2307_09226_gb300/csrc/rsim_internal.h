@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -52,6 +53,28 @@ struct FrameIO {
   int64_t bimg_nch;           // chunk capacity of bimg per column tile
   int32_t splits;             // pixel splits of the contraction
   int32_t pad;
+};
+
+// NVTX range in the "rsim" domain for the lifetime of a scope (header-only NVTX v3: it
+// costs a few nanoseconds unless a profiler is attached).  The ranges mark the host-side
+// launches of each stage and of each served request, so a profiler's kernel list can be
+// split by stage and by request (e.g. ncu --nvtx --nvtx-include "rsim@request 17/").
+inline nvtxDomainHandle_t nvtx_domain() {
+  static nvtxDomainHandle_t d = nvtxDomainCreateA("rsim");
+  return d;
+}
+struct NvtxRange {
+  explicit NvtxRange(const char* msg) {
+    nvtxEventAttributes_t a = {};
+    a.version = NVTX_VERSION;
+    a.size = NVTX_EVENT_ATTRIB_STRUCT_SIZE;
+    a.messageType = NVTX_MESSAGE_TYPE_ASCII;
+    a.message.ascii = msg;
+    nvtxDomainRangePushEx(nvtx_domain(), &a);
+  }
+  ~NvtxRange() { nvtxDomainRangePop(nvtx_domain()); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // Device status word bits (OR-ed by kernels, read by rsim_sync_status).

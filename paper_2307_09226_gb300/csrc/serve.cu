@@ -17,6 +17,7 @@
 // function enqueued after the request's kernels, which stamps the latency and
 // wakes the scheduler and any waiter.
 #include <cuda_runtime.h>
+#include <stdio.h>
 
 #include <algorithm>
 #include <chrono>
@@ -207,6 +208,9 @@ bool admit_one(rsim_server* s) {
   s->in_flight++;
   s->stats.peak_in_flight = std::max(s->stats.peak_in_flight, s->in_flight);
   void* cubes[1] = {r.r.cube};
+  char what[64];
+  snprintf(what, sizeof what, "request %llu", (unsigned long long)r.ticket);
+  NvtxRange request_range(what);
   rsim_status st = run_frames(s->ctx, (char*)r.ws, r.bytes, r.k, &r.r.pixels, 1, cubes, r.r.tier,
                               r.r.out_dtype, r.plan, sl.status, rs);
   // P_valid of this request, read by retire() once the stream reaches it

@@ -20,12 +20,28 @@ Conventions
 """
 from __future__ import annotations
 
+import json
+import os
 from dataclasses import dataclass, field, replace
+from functools import lru_cache
 from typing import Dict, List
 
 import numpy as np
 
 C_LIGHT = 299_792_458.0
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs")
+
+
+@lru_cache(maxsize=None)
+def _config_text(n: int) -> str:
+    with open(os.path.join(CONFIG_DIR, f"config{n}.json")) as f:
+        return f.read()
+
+
+def load_config(n: int) -> Dict:
+    """The parameters of workload n (1..5) from configs/config<n>.json: radar, pixel grid,
+    value distributions, mask fraction, seeds and (config 5) the serving mix."""
+    return json.loads(_config_text(n))
 
 
 @dataclass(frozen=True)
@@ -136,18 +152,27 @@ def random_frame(radar: Radar, n_az: int, n_el: int, seed: int, mask_frac: float
 # that stand in for the paper's Blender scene (Section III).
 # ----------------------------------------------------------------------------------
 
-def config1(seed: int = 1) -> Frame:
-    """One small frame: M=2, N=4, Ns=64, L=32, 32x32 pixels, FP64 buffers, complex128 out."""
-    radar = Radar(M=2, N=4, Ns=64, L=32)
-    px = random_frame(radar, 32, 32, seed, mask_frac=0.0, dtype=np.float64)
-    return Frame(radar, px, "complex128", {"workload": "frame-32x32-V8-Ns64-L32"})
+def _frame_from_config(n: int, seed=None) -> Frame:
+    c = load_config(n)
+    radar = Radar(**c["radar"])
+    p = c["pixels"]
+    assert p["log_abs_sigma"] == [0.0, 1.0] and c["grid"]["az_deg"] == [-60, 60] and c["grid"]["el_deg"] == [-30, 30]
+    px = random_frame(radar, c["grid"]["n_az"], c["grid"]["n_el"], c["seed"] if seed is None else seed,
+                      mask_frac=p["mask_frac"], dtype=np.dtype(c["pixel_dtype"]).type, r_lo=p["range_m"][0],
+                      r_hi=p["range_m"][1], v_max=p["vel_max_m_s"])
+    return Frame(radar, px, c["out_dtype"], {"workload": c["workload"]})
 
 
-def config2(seed: int = 2) -> Frame:
-    """One frame: M=3, N=4, Ns=256, L=128, 256x256 pixels, 30% background, complex64 out."""
-    radar = Radar(M=3, N=4, Ns=256, L=128)
-    px = random_frame(radar, 256, 256, seed, mask_frac=0.30, dtype=np.float32)
-    return Frame(radar, px, "complex64", {"workload": "frame-256x256-V12-Ns256-L128-mask30"})
+def config1(seed: int = None) -> Frame:
+    """One small frame (configs/config1.json): M=2, N=4, Ns=64, L=32, 32x32 pixels, FP64
+    buffers, complex128 out."""
+    return _frame_from_config(1, seed)
+
+
+def config2(seed: int = None) -> Frame:
+    """One frame (configs/config2.json): M=3, N=4, Ns=256, L=128, 256x256 pixels, 30%
+    background, complex64 out."""
+    return _frame_from_config(2, seed)
 
 
 def parity_frame(seed: int = 11, M=2, N=3, Ns=96, L=48, n_az=71, n_el=70,
@@ -158,9 +183,10 @@ def parity_frame(seed: int = 11, M=2, N=3, Ns=96, L=48, n_az=71, n_el=70,
     return Frame(radar, px, "complex64", {"workload": f"parity-{n_az}x{n_el}-V{M*N}-Ns{Ns}-L{L}"})
 
 
-def walking_batch(n_frames: int = 64, seed: int = 4, n_az: int = 256, n_el: int = 256,
-                  dtype=np.float32) -> List[Frame]:
-    """Animation of a walking-pedestrian-like scene in front of a static wall.
+def walking_batch(n_frames: int = None, seed: int = None, n_az: int = None, n_el: int = None,
+                  dtype=None) -> List[Frame]:
+    """Animation of a walking-pedestrian-like scene in front of a static wall
+    (configs/config4.json; the arguments override its frame count, seed, grid and dtype).
 
     Per frame f: a pedestrian cluster of n_f ~ U{2000..20000} pixels in a contiguous
     az/el window whose centre moves as 40 deg * sin(2 pi f / 64); its range is
@@ -169,8 +195,15 @@ def walking_batch(n_frames: int = 64, seed: int = 4, n_az: int = 256, n_el: int 
     A wall of w_f ~ U{0..45000} pixels sits at R = min(6 / (cos az cos el), 8) m with
     v = 0 and |sigma| = exp(N(-1, 0.5)).  Everything else is a background miss.
     """
+    c = load_config(4)
+    n_frames = c["frames"] if n_frames is None else n_frames
+    seed = c["seed"] if seed is None else seed
+    n_az = c["grid"]["n_az"] if n_az is None else n_az
+    n_el = c["grid"]["n_el"] if n_el is None else n_el
+    dtype = np.dtype(c["pixel_dtype"]).type if dtype is None else dtype
+    ped_c, wall_c = c["pedestrian"], c["wall"]
     rng = np.random.default_rng(seed)
-    radar = Radar(M=3, N=4, Ns=256, L=128)
+    radar = Radar(**c["radar"])
     P = n_az * n_el
     az, el = grid_angles(n_az, n_el)
     frames = []
@@ -180,13 +213,13 @@ def walking_batch(n_frames: int = 64, seed: int = 4, n_az: int = 256, n_el: int 
         sim = np.zeros(P)
         vel = np.zeros(P)
         # wall: a random set of grid cells not covered by the pedestrian
-        n_ped = int(rng.integers(2000, 20001))
-        n_wall = int(rng.integers(0, 45001))
+        n_ped = int(rng.integers(ped_c["pixels"][0], ped_c["pixels"][1] + 1))
+        n_wall = int(rng.integers(wall_c["pixels"][0], wall_c["pixels"][1] + 1))
         ph = 2.0 * np.pi * f / 64.0
-        az_c = np.deg2rad(40.0 * np.sin(ph))
+        az_c = np.deg2rad(ped_c["az_swing_deg"] * np.sin(ph))
         i_c = int(np.clip(np.round((np.rad2deg(az_c) + 60.0) / 120.0 * n_az - 0.5), 0, n_az - 1))
         # pedestrian window: tall (el) and narrow (az), height:width about 2.5:1
-        w = max(1, int(np.round(np.sqrt(n_ped / 2.5))))
+        w = max(1, int(np.round(np.sqrt(n_ped / ped_c["aspect_el_over_az"]))))
         h = int(np.ceil(n_ped / w))
         h = min(h, n_el)
         w = min(int(np.ceil(n_ped / h)), n_az)
@@ -194,30 +227,31 @@ def walking_batch(n_frames: int = 64, seed: int = 4, n_az: int = 256, n_el: int 
         j0 = int(np.clip(n_el // 2 - h // 2, 0, n_el - h))
         jj, ii = np.meshgrid(np.arange(j0, j0 + h), np.arange(i0, i0 + w), indexing="ij")
         ped = (jj * n_az + ii).ravel()[:n_ped]
-        r_f = 3.0 + 2.0 * np.sin(ph + 0.7)
-        rr[ped] = r_f + rng.uniform(-0.3, 0.3, ped.size)
-        vel[ped] = np.clip(1.5 * np.sin(ph) + rng.uniform(-1.5, 1.5, ped.size), -3.0, 3.0)
+        r_f = ped_c["range_centre_m"] + ped_c["range_swing_m"] * np.sin(ph + ped_c["range_phase"])
+        jit, vt, vl, vc = ped_c["range_jitter_m"], ped_c["torso_m_s"], ped_c["limb_m_s"], ped_c["vel_clip_m_s"]
+        rr[ped] = r_f + rng.uniform(-jit, jit, ped.size)
+        vel[ped] = np.clip(vt * np.sin(ph) + rng.uniform(-vl, vl, ped.size), -vc, vc)
         a, b = _strength(rng, ped.size)
         sre[ped], sim[ped] = a, b
         free = np.setdiff1d(np.arange(P), ped, assume_unique=True)
         wall = np.sort(rng.choice(free, size=min(n_wall, free.size), replace=False))
-        rr[wall] = np.minimum(6.0 / (np.cos(az[wall]) * np.cos(el[wall])), 8.0)
-        a, b = _strength(rng, wall.size, mean=-1.0, sd=0.5)
+        rr[wall] = np.minimum(wall_c["range_m"] / (np.cos(az[wall]) * np.cos(el[wall])), wall_c["range_cap_m"])
+        a, b = _strength(rng, wall.size, mean=wall_c["log_abs_sigma"][0], sd=wall_c["log_abs_sigma"][1])
         sre[wall], sim[wall] = a, b
         px = Pixels(rr, sre, sim, az.copy(), el.copy(), vel).astype(dtype)
         frames.append(Frame(radar, px, "complex64",
                             {"workload": "walking-256x256-V12-Ns256-L128", "frame": f,
-                             "v_torso": 1.5 * np.sin(ph), "n_ped": int(ped.size),
+                             "v_torso": vt * np.sin(ph), "n_ped": int(ped.size),
                              "n_wall": int(wall.size)}))
     return frames
 
 
-SERVE_CHOICES = dict(M=(2, 3, 4), N=(4, 8, 12), Ns=(128, 256, 512), L=(64, 128, 256),
-                     grid=(64, 128, 256, 512), tier=("fp32", "split_bf16"))
+SERVE_CHOICES = {k: tuple(v) for k, v in load_config(5)["choices"].items()}
 
 
 def serving_requests(n: int, seed: int = 5, grids=None, tiers=None) -> List[Dict]:
-    """Request mix for the serving loop: uniform choices of radar and image size.
+    """Request mix for the serving loop (configs/config5.json): uniform choices of radar
+    and image size.
 
     Each request is a dict with a Radar, a grid edge and an accuracy tier; the pixel
     buffers are drawn lazily by ``request_frame`` (seed derived from the request id).
@@ -228,7 +262,8 @@ def serving_requests(n: int, seed: int = 5, grids=None, tiers=None) -> List[Dict
     out = []
     for k in range(n):
         radar = Radar(M=int(rng.choice(SERVE_CHOICES["M"])), N=int(rng.choice(SERVE_CHOICES["N"])),
-                      Ns=int(rng.choice(SERVE_CHOICES["Ns"])), L=int(rng.choice(SERVE_CHOICES["L"])))
+                      Ns=int(rng.choice(SERVE_CHOICES["Ns"])), L=int(rng.choice(SERVE_CHOICES["L"])),
+                      **load_config(5)["radar"])
         g = int(rng.choice(grids))
         t = str(rng.choice(tiers))
         out.append({"id": k, "radar": radar, "grid": g, "tier": t, "seed": seed * 1_000_003 + k})
@@ -236,7 +271,9 @@ def serving_requests(n: int, seed: int = 5, grids=None, tiers=None) -> List[Dict
 
 
 def request_frame(req: Dict, dtype=np.float32) -> Frame:
-    px = random_frame(req["radar"], req["grid"], req["grid"], req["seed"], mask_frac=0.30, dtype=dtype)
+    p = load_config(5)["pixels"]
+    px = random_frame(req["radar"], req["grid"], req["grid"], req["seed"], mask_frac=p["mask_frac"], dtype=dtype,
+                      r_lo=p["range_m"][0], r_hi=p["range_m"][1], v_max=p["vel_max_m_s"])
     return Frame(req["radar"], px, "complex64", {"workload": "serve", "id": req["id"]})
 
 

@@ -37,7 +37,9 @@ def _ambiguous(scene, az, el, which, eps=2e-5):
 def _compare(scene, got, want, rtol_r, rtol_s, atol_v, max_ambiguous=0.01):
     R, Rw = got["range"].astype(np.float64), want["range"]
     hit_g, hit_w = np.isfinite(R), np.isfinite(Rw)
-    close_r = np.where(hit_w & hit_g, np.abs(R - Rw) <= rtol_r * Rw, hit_g == hit_w)
+    both = hit_w & hit_g
+    close_r = hit_g == hit_w  # a miss (inf) must be a miss on both sides ...
+    close_r[both] = np.abs(R[both] - Rw[both]) <= rtol_r * Rw[both]  # ... and hits agree in range
     smax = max(want["sigma_re"].max(), 1e-30)
     close_s = np.abs(got["sigma_re"] - want["sigma_re"]) <= rtol_s * np.maximum(want["sigma_re"], 1e-3 * smax)
     close_v = np.abs(got["vel"] - want["vel"]) <= atol_v

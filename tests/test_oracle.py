@@ -342,3 +342,29 @@ def test_range_doppler_peak_recovers_range_and_velocity():
 
 def test_e_velo_is_the_mean_absolute_error():
     assert oracle.e_velo([1.0, -2.0, 0.5], [1.5, -1.0, 0.5]) == pytest.approx(0.5)
+
+
+def test_workload_config_files_drive_the_generator():
+    """configs/config<n>.json hold the five workloads; the generator follows them."""
+    from paper_2307_09226_gb300 import synth
+    for n in range(1, 6):
+        c = synth.load_config(n)
+        assert c["name"] == f"config{n}"
+    for n, make in ((1, synth.config1), (2, synth.config2)):
+        c = synth.load_config(n)
+        f = make()
+        assert f.pixels.P == c["grid"]["n_az"] * c["grid"]["n_el"]
+        assert (f.radar.M, f.radar.N, f.radar.Ns, f.radar.L) == tuple(c["radar"][k] for k in ("M", "N", "Ns", "L"))
+        assert f.pixels.dtype == np.dtype(c["pixel_dtype"]) and f.out_dtype == c["out_dtype"]
+        miss = np.mean((f.pixels.sigma_re == 0) & (f.pixels.sigma_im == 0))
+        assert abs(miss - c["pixels"]["mask_frac"]) < 0.02
+    c4 = synth.load_config(4)
+    frames = synth.walking_batch(n_frames=3)
+    for f in frames:
+        assert c4["pedestrian"]["pixels"][0] <= f.meta["n_ped"] <= c4["pedestrian"]["pixels"][1]
+        assert f.meta["n_wall"] <= c4["wall"]["pixels"][1]
+    c5 = synth.load_config(5)
+    reqs = synth.serving_requests(50)
+    for r in reqs:
+        assert r["radar"].M in c5["choices"]["M"] and r["radar"].L in c5["choices"]["L"]
+        assert r["grid"] in c5["choices"]["grid"] and r["tier"] in c5["choices"]["tier"]

@@ -40,15 +40,19 @@ def test_static_entry_matches_rsim_synth_twice(env, tier, maker):
     ref = ctx.synth(f.radar, px, tier).cpu().numpy()
     assert ctx.sync_status() == _abi.OK
     status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    cubes = [torch.full((f.radar.V, f.radar.Ns, f.radar.L), float("nan"), dtype=torch.complex64,
+                        device="cuda") for _ in range(2)]
     outs = []
-    for _ in range(2):
-        cube = torch.full((f.radar.V, f.radar.Ns, f.radar.L), float("nan"), dtype=torch.complex64,
-                          device="cuda")
-        rc = _abi.rsim_synth_static(f.radar, px, _abi.TIERS[tier], cube, device_status=status)
+    for i in range(2):
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        rc = _abi.rsim_synth_static(f.radar, px, _abi.TIERS[tier], cubes[i], device_status=status)
         assert rc == _abi.OK, _abi.last_error()
         torch.cuda.synchronize()
+        if i == 1:  # after the first call has loaded the kernels: no device memory taken
+            assert torch.cuda.mem_get_info()[0] == free_before
         assert int(status.item()) == 0
-        outs.append(cube.cpu().numpy())
+        outs.append(cubes[i].cpu().numpy())
     for got in outs:
         assert np.all(np.isfinite(got))
         assert oracle.rel_l2(got, ref) <= TOL[tier]
