@@ -343,6 +343,15 @@ rsim_status rsim_sync_status(rsim_ctx* ctx, rsim_stream stream);
  * Errors: INVALID_ARG (NULL ctx, limit out of range), CUDA. */
 rsim_status rsim_selftest_wait_timeout(rsim_ctx* ctx, uint64_t limit_ns, rsim_stream stream);
 
+/* Measurement helper for benchmarks (no counterpart in the paper): the rate, in lane
+ * operations per second, at which this device performs non-returning 32-bit integer
+ * atomic additions to shared memory without bank conflicts, at the NUFFT spreading
+ * kernel's occupancy and access pattern.  That unit bounds the spreading kernel, so the
+ * rate is its roofline denominator.  Runs a probe kernel six times on `stream` (the first
+ * as a warm-up) and returns the best; synchronous.  Allocates nothing.
+ * Errors: INVALID_ARG, CUDA. */
+rsim_status rsim_measure_smem_atomics(rsim_ctx* ctx, double* lane_ops_per_s, rsim_stream stream);
+
 /* Stage timing for benchmarks.  While profiling is on, every rsim_synth /
  * rsim_synth_batch call records CUDA events on its stream around its three stages
  * (compaction + FP64 phases, contraction, split reduction), and around the main kernel

@@ -138,6 +138,7 @@ SIGNATURES = {
                                    c_void_p, c_void_p, c_void_p, c_int32, c_void_p]),
     "rsim_sync_status": (c_int, [c_void_p, c_void_p]),
     "rsim_selftest_wait_timeout": (c_int, [c_void_p, c_uint64, c_void_p]),
+    "rsim_measure_smem_atomics": (c_int, [c_void_p, POINTER(c_double), c_void_p]),
     "rsim_autotune": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
                               POINTER(rsim_plan), c_void_p]),
     "rsim_raycast": (c_int, [c_void_p, POINTER(rsim_camera), POINTER(rsim_primitive), c_int32,
@@ -363,6 +364,13 @@ def rsim_raycast(ctx, scene, n_az, n_el, fov, out, falloff=True, stream=None):
 
 def rsim_profile_enable(ctx, on: bool):
     check(load().rsim_profile_enable(ctx, 1 if on else 0))
+
+
+def rsim_measure_smem_atomics(ctx, stream=None) -> float:
+    """Measured shared-memory atomic rate of the device (lane operations per second)."""
+    v = c_double()
+    check(load().rsim_measure_smem_atomics(ctx, ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def rsim_profile_read(ctx) -> rsim_profile:

@@ -76,6 +76,14 @@ __device__ __forceinline__ float es_kernel(float z, float beta) {
   return z2 < 1.f ? expf(beta * (sqrtf(1.f - z2) - 1.f)) : 0.f;
 }
 
+// The same with the hardware exponential and reciprocal square root, for the spreading
+// weights: sqrt(x) = x rsqrt(x) for x = 1 - z^2 in (0, 1]; a few ulp per weight, far below
+// the kernel's own truncation error (the deconvolution factors keep es_kernel).
+__device__ __forceinline__ float es_kernel_fast(float z, float beta) {
+  const float x = 1.f - z * z;
+  return x > 0.f ? __expf(beta * (x * rsqrtf(x) - 1.f)) : 0.f;
+}
+
 // Nearest grid cell of a position (mod G, G a power of two) and the offset of the
 // position from it, in [-1/2, 1/2) cells: X = xq G / 2^32.
 __device__ __forceinline__ void nearest_cell(uint32_t xq, int G, int& c, float& d) {
@@ -110,13 +118,20 @@ __device__ __forceinline__ float grid_scale(const FrameIO& fr, bool inverse) {
   return inverse ? ldexpf(m, -30) : ldexpf(1.f, 30) / m;
 }
 
-// Add a 32-bit signed term to a sum kept as two 32-bit words with non-returning
-// atomics: the low 16 bits of each term go to `lo` (unsigned) and the signed high part
-// to `hi`, so the sum is hi 2^16 + lo exactly while a word receives fewer than 2^16
-// terms (a work item holds kSpreadChunk records, each adding once per cell).
+// Add a 32-bit signed term v to a sum kept as two 32-bit words with non-returning
+// atomics: `lo` takes v itself (wrapping mod 2^32) and `hi` its signed high part
+// v >> 16.  With H = sum of (v >> 16) and LO = sum of v mod 2^32, the sum of the low
+// halves v & 0xffff is (LO - H 2^16) mod 2^32, and the exact sum is H 2^16 plus that
+// (join_split), while a word receives fewer than 2^16 terms (a work item holds
+// kSpreadChunk records, each adding once per cell): then |H| < 2^31 and the low halves
+// sum below 2^32.
 __device__ __forceinline__ void add_split(unsigned* lo, int* hi, int v) {
-  atomicAdd(lo, (unsigned)(v & 0xffff));
+  atomicAdd(lo, (unsigned)v);
   atomicAdd(hi, v >> 16);
+}
+__device__ __forceinline__ long long join_split(unsigned lo, int hi) {
+  const unsigned low_halves = lo - ((unsigned)hi << 16);
+  return (long long)hi * 65536ll + (long long)low_halves;
 }
 
 // Twiddle e of an FFT plan: entry j ns + k of pass p is exp(+j 2 pi j k / (ns R)).
@@ -466,11 +481,13 @@ __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __res
         // the nearest cell lies in this tile: local padded coordinates of the first tap
         const int lx = cx - tx * g.Tx + H + sx, ly = cy - ty * g.Ty + H + sy;
         const float qr = q.q.x * scale, qi = q.q.y * scale;
+        // tap j sits at z = (s + j - d) 2 / W in kernel units
+        const float zx0 = ((float)sx - dx) * k2w, zy0 = ((float)sy - dy) * k2w;
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-          const float wx = es_kernel(((float)(sx + j) - dx) * k2w, beta);
+          const float wx = es_kernel_fast(fmaf((float)j, k2w, zx0), beta);
           s_ax[warp][j][lane] = make_float2(qr * wx, qi * wx);
-          s_wy[warp][j][lane] = es_kernel(((float)(sy + j) - dy) * k2w, beta);
+          s_wy[warp][j][lane] = es_kernel_fast(fmaf((float)j, k2w, zy0), beta);
         }
         s_base[warp][lane] = lx * STRIDE + ly;
       }
@@ -488,8 +505,8 @@ __global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __res
     const int64_t gbase = (int64_t)v * g.Gx * g.Gy;
     for (int i = threadIdx.x; i < PAD * PAD; i += blockDim.x) {
       const int row = i / PAD, col = i % PAD, at = row * STRIDE + col;
-      const long long re = ((long long)hi_re[at] << 16) + (long long)lo_re[at];
-      const long long im = ((long long)hi_im[at] << 16) + (long long)lo_im[at];
+      const long long re = join_split(lo_re[at], hi_re[at]);
+      const long long im = join_split(lo_im[at], hi_im[at]);
       if (re == 0 && im == 0) continue;
       const int gx = (x0 + row) & (g.Gx - 1), gy = (y0 + col) & (g.Gy - 1);
       unsigned long long* cell = grid + 2 * (gbase + (int64_t)gx * g.Gy + gy);

@@ -58,7 +58,7 @@ struct FrameIO {
 // NVTX range in the "rsim" domain for the lifetime of a scope (header-only NVTX v3: it
 // costs a few nanoseconds unless a profiler is attached).  The ranges mark the host-side
 // launches of each stage and of each served request, so a profiler's kernel list can be
-// split by stage and by request (e.g. ncu --nvtx --nvtx-include "rsim@request 17/").
+// split by stage and by request (ncu's --nvtx range filters select one range's kernels).
 inline nvtxDomainHandle_t nvtx_domain() {
   static nvtxDomainHandle_t d = nvtxDomainCreateA("rsim");
   return d;

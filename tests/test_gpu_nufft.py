@@ -122,3 +122,12 @@ def test_unsupported_axes(ctx, Ns, L):
     with pytest.raises(_abi.RsimError) as e:
         ctx.synth(r, device.upload(px), "nufft")
     assert e.value.status == _abi.ERR_UNSUPPORTED
+
+
+def test_shared_atomic_rate_probe(ctx):
+    """The measured shared-memory atomic rate (the spreading kernel's roofline denominator)
+    is a plausible number for a GPU of this size: above 1e12 and at most the one
+    32-lane-wavefront-per-clock figure at a 2.1 GHz clock on 152 SMs, with headroom."""
+    rate = _abi.rsim_measure_smem_atomics(ctx.h)
+    print(f"shared atomics: {rate / 1e12:.3f} T lane-op/s")
+    assert 1e12 < rate < 1.2 * 152 * 32 * 2.1e9
