@@ -21,7 +21,7 @@
 //                 builds the geometry's tables: 1 / (Psi_x(n') Psi_y(l')) (one warp per
 //                 mode, a 128-node midpoint rule of Psi(k) = (w/2) int phi(z) cos(pi k w z
 //                 / G) dz) and the twiddles of both FFTs.  The last counting block scans
-//                 the counts and cuts every bin into work items of 256 records;
+//                 the counts and cuts every bin into work items of 512 records;
 //   nu_bin_fill   records (x, y, q') stored bin by bin (one global reservation per
 //                 (block, bin), ranks within the block from shared memory);
 //   nu_spread     persistent CTAs take the work items in turn; a warp takes one record
@@ -50,7 +50,7 @@ constexpr int kNWMin = 4, kNWMax = 8;       // kernel widths in cells (the defau
 constexpr float kNBetaPerW = 2.30f;         // ES shape beta = 2.30 w for an oversampling of 2
 constexpr int kNTile = 32;                  // grid cells per tile side
 constexpr int kNQuad = 128;                 // midpoint nodes for Psi
-constexpr int kSpreadChunk = 256;           // records per spreading work item
+constexpr int kSpreadChunk = 512;           // records per spreading work item
 constexpr int kBinThreads = 256;            // binning blocks: one channel, kBinItems points
 constexpr int kBinItems = 4 * kBinThreads;
 static_assert(kBinThreads % 32 == 0 && kBinThreads <= 1024, "binning blocks are whole warps");
@@ -381,9 +381,9 @@ __global__ void __launch_bounds__(kBinThreads) nu_bin_fill(const FrameIO* __rest
 // once per record (one lane per record) and staged per warp: (q'_re, q'_im) psi_x by jx,
 // psi_y by jy.  All of it sits in dynamic shared memory:
 //   [lo re | lo im | hi re | hi im] tile words, then the staging, then a zero row.
-constexpr int kSpreadThreads = 256;
+constexpr int kSpreadThreads = 512;
 constexpr int kSpreadWarps = kSpreadThreads / 32;
-constexpr int kSpreadBlocksPerSm = 4;  // persistent CTAs per SM (shared memory: <= 53 KB each)
+constexpr int kSpreadBlocksPerSm = 3;  // persistent CTAs per SM (about 70 KB of shared memory each at w = 7)
 constexpr int kStageLd = 33;           // staged values of 32 records per jx (or jy), padded
 
 template <int W>
@@ -407,7 +407,7 @@ struct SpreadLayout {
 
 // Persistent CTAs take the work items in turn (their number is known on the device only).
 template <int W>
-__global__ void __launch_bounds__(kSpreadThreads) nu_spread(const FrameIO* __restrict__ fp, NuGeo g,
+__global__ void __launch_bounds__(kSpreadThreads, kSpreadBlocksPerSm) nu_spread(const FrameIO* __restrict__ fp, NuGeo g,
                                                             const int* __restrict__ off,
                                                             const int* __restrict__ items,
                                                             const int* __restrict__ item_bin,
