@@ -164,7 +164,7 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
 
 // cube = scale * sum over splits s = 0, 1, ... (in this order) of partial[s], with
 // compensated FP32 additions (GB300's FP64 rate is a small fraction of its FP32 rate).
-// Loads of eight splits are issued together; the additions keep the split order.
+// Loads of kReduceBatch splits are issued together; the additions keep the split order.
 __global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, int splits,
                              int out_dtype, int scale_mode) {
   wait_prior_grid();
@@ -178,13 +178,13 @@ __global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, 
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
     float re = 0.f, im = 0.f, cre = 0.f, cim = 0.f;
-    for (int s0 = 0; s0 < splits; s0 += 8) {
-      float2 p[8];
+    for (int s0 = 0; s0 < splits; s0 += kReduceBatch) {
+      float2 p[kReduceBatch];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
+      for (int j = 0; j < kReduceBatch; ++j)
         p[j] = (s0 + j < splits) ? __ldcs(part + (int64_t)(s0 + j) * count + i) : make_float2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < kReduceBatch; ++j) {
         if (s0 + j < splits) {
           kahan_add(re, cre, p[j].x);
           kahan_add(im, cim, p[j].y);

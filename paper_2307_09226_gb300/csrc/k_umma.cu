@@ -708,8 +708,9 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
 
 // cube = scale * sum over splits s = 0, 1, ... (in this order) of the tiled partial
 // sums, with compensated FP32 additions per component.  One thread per (accumulator
-// row, column pair) of a tile: the loads of consecutive threads are contiguous.  Eight
-// splits' loads are issued together; the additions keep the split order.
+// row, column pair) of a tile: the loads of consecutive threads are contiguous.  The
+// loads of kReduceBatch splits are issued together (a frame's splits in one or two round
+// trips to memory); the additions keep the split order.
 __global__ void split_reduce_tiles(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles,
                                    int64_t sstride, int splits, int out_dtype, int scale_mode) {
   wait_prior_grid();
@@ -732,13 +733,13 @@ __global__ void split_reduce_tiles(const FrameIO* __restrict__ frames, Consts k,
     const int l = (int)(tile % ntiles) * NT + 2 * pr;
     if (row >= rows || l >= k.L) continue;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-    for (int b = 0; b < splits; b += 8) {
-      float4 p[8];
+    for (int b = 0; b < splits; b += kReduceBatch) {
+      float4 p[kReduceBatch];
 #pragma unroll
-      for (int j = 0; j < 8; ++j)
+      for (int j = 0; j < kReduceBatch; ++j)
         p[j] = (b + j < splits) ? __ldcs(part + (int64_t)(b + j) * n4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
+      for (int j = 0; j < kReduceBatch; ++j) {
         if (b + j < splits) {
           kahan_add(s0, c0, p[j].x);
           kahan_add(s1, c1, p[j].y);

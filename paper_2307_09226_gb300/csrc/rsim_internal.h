@@ -15,6 +15,7 @@ constexpr int kChunkPx = 32;        // pixels per pipeline stage / K-chunk (64 r
 constexpr int kPrepTile = 256;      // pixels per block of the compaction kernels
 constexpr int kPrepThreads = 256;
 constexpr int kMaxSplits = 64;
+constexpr int kReduceBatch = 16;    // split partials a reduction thread loads at once
 
 // Host-resolved constants of one radar configuration.  The per-pixel FP64 phase
 // increments are products of these with R, u and vel (Eq. 1 / Eq. 2):
