@@ -1,4 +1,4 @@
-// FP32 direct sum of Eq. 2 on CUDA cores, and the ordered split reduction.
+// FP32 direct sum of Eq. 2 on CUDA cores.
 //
 // The phase of Eq. 2 separates into a fast-time/channel part a_{p,v} n + c_{p,v} and a
 // slow-time part b_p l, so each cube entry is
@@ -17,7 +17,7 @@
 namespace rsim {
 namespace {
 
-constexpr int kTL = 64;       // l per tile
+constexpr int kTL = kDirectTileL;  // l per tile
 constexpr int kThreads = 256;
 
 // exp(j 2 pi x) for a 2^-32-cycle fixed-point phase.  The phase is reinterpreted as
@@ -162,44 +162,6 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
   }
 }
 
-// cube = scale * sum over splits s = 0, 1, ... (in this order) of partial[s], with
-// compensated FP32 additions (GB300's FP64 rate is a small fraction of its FP32 rate).
-// Loads of kReduceBatch splits are issued together; the additions keep the split order.
-__global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, int splits,
-                             int out_dtype, int scale_mode) {
-  wait_prior_grid();
-  const FrameIO& fr = frames[blockIdx.y];
-  float scale = 1.f;
-  if (scale_mode) {
-    const float m = __uint_as_float((unsigned)fr.meta[1]);
-    scale = (m > 0.f) ? ldexpf(1.f, ilogbf(m) + 1) : 1.f;
-  }
-  const float2* __restrict__ part = fr.partial;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    float re = 0.f, im = 0.f, cre = 0.f, cim = 0.f;
-    for (int s0 = 0; s0 < splits; s0 += kReduceBatch) {
-      float2 p[kReduceBatch];
-#pragma unroll
-      for (int j = 0; j < kReduceBatch; ++j)
-        p[j] = (s0 + j < splits) ? __ldcs(part + (int64_t)(s0 + j) * count + i) : make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < kReduceBatch; ++j) {
-        if (s0 + j < splits) {
-          kahan_add(re, cre, p[j].x);
-          kahan_add(im, cim, p[j].y);
-        }
-      }
-    }
-    re *= scale;  // power of two: exact
-    im *= scale;
-    if (out_dtype == RSIM_C128)
-      reinterpret_cast<double2*>(fr.cube)[i] = make_double2((double)re, (double)im);
-    else
-      reinterpret_cast<float2*>(fr.cube)[i] = make_float2(re, im);
-  }
-}
-
 }  // namespace
 
 namespace {
@@ -224,124 +186,6 @@ cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int spl
   if (tile_n == 64) return launch_direct_t<64>(k, frames, F, splits, out_dtype, st);
   if (tile_n == 128) return launch_direct_t<128>(k, frames, F, splits, out_dtype, st);
   return cudaErrorInvalidValue;
-}
-
-cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int splits, int out_dtype,
-                          float scale_mode, cudaStream_t st) {
-  const int64_t count = (int64_t)k.V * k.Ns * k.L;
-  if (count <= 0 || F <= 0) return cudaSuccess;
-  int64_t blocks = (count + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  dim3 grid((unsigned)blocks, F);
-  return launch_dependent(split_reduce, grid, dim3(256), 0, st, frames, count, splits, out_dtype,
-                          scale_mode != 0.f ? 1 : 0);
-}
-
-bool uses_partial(int tier, int64_t P, int splits, int group) {
-  if (tier == RSIM_TIER_NUFFT) return false;
-  if (splits > 1) return true;
-  if (tier == RSIM_TIER_FP32) return false;
-  const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
-  return chunks > group;
-}
-
-int group_chunks(int tier) {
-  return (tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16) ? 40 : 96;
-}
-
-// The split tiers' 2e-5 bar leaves room for the round-toward-zero bias of at most 40
-// chunks (480 accumulating MMAs, a relative shrink of about 1e-5); the plain 16-bit tiers
-// (1e-2) allow 384 chunks (1536 MMAs, about 3e-5).
-int group_chunks_max(int tier) {
-  return (tier == RSIM_TIER_SPLIT_BF16 || tier == RSIM_TIER_SPLIT_FP16) ? 40 : 384;
-}
-
-int units_per_split(int tier, int V, int Ns, int L, int tile_n) {
-  if (tier == RSIM_TIER_FP32) return V * ((Ns + tile_n - 1) / tile_n) * ((L + kTL - 1) / kTL);
-  const int64_t rows = (int64_t)V * Ns;
-  const int nt = (L + tile_n - 1) / tile_n;
-  return (int)(((rows + 127) / 128) * nt);
-}
-
-int default_splits(int tier, int V, int Ns, int L, int tile_n, int64_t P, int num_sms) {
-  if (tier == RSIM_TIER_NUFFT) return 1;
-  const int tiles = units_per_split(tier, V, Ns, L, tile_n);
-  const int64_t chunks = (P + kChunkPx - 1) / kChunkPx;
-  // keep at least 8 chunks (256 pixels) per split
-  int64_t smax = chunks / 8 > 0 ? chunks / 8 : 1;
-  if (smax > kMaxSplits) smax = kMaxSplits;
-  if (tier == RSIM_TIER_FP32) {
-    // FP32 accumulation: at most 8192 pixels per split, so that the running sum of
-    // random-phase terms keeps a relative rounding error of a few 1e-6 (the splits are
-    // then added with compensated sums); above that, the split count that fills whole
-    // waves of two resident CTAs per SM best
-    const int64_t smin = std::min<int64_t>(std::max<int64_t>((P + 8191) / 8192, 1), kMaxSplits);
-    const int64_t slots = 2ll * num_sms;
-    double best = -1.0;
-    int64_t bs = smin;
-    for (int64_t s = smin; s <= std::max(smin, smax); ++s) {
-      const int64_t units = (int64_t)tiles * s;
-      const int64_t waves = (units + slots - 1) / slots;
-      const double eff = (double)units / (double)(waves * slots) - 0.001 * s;
-      if (eff > best + 1e-9) {
-        best = eff;
-        bs = s;
-      }
-    }
-    return (int)bs;
-  }
-  // tensor tiers: one persistent CTA per SM takes equal units from a counter; pick the
-  // split count whose unit count fills whole rounds of SMs best, with a small cost per
-  // split for the partial buffer it adds
-  double best = -1.0;
-  int bs = 1;
-  for (int s = 1; s <= smax; ++s) {
-    const int64_t units = (int64_t)tiles * s;
-    const int64_t rounds = (units + num_sms - 1) / num_sms;
-    const double eff = (double)units / (double)(rounds * num_sms) - 0.003 * s;
-    if (eff > best + 1e-9) {
-      best = eff;
-      bs = s;
-    }
-  }
-  return bs;
-}
-
-void resolve_tile(int tier, const Consts& k, rsim_plan* p) {
-  if (tier == RSIM_TIER_FP32) {
-    if (p->tile_n == 0) p->tile_n = kDirectTileN;
-    p->group_chunks = 0;
-  } else if (tensor_tier(tier)) {
-    if (p->tile_n == 0) p->tile_n = tile_nt(k.L);
-    if (p->group_chunks == 0) p->group_chunks = group_chunks(tier);
-  } else {
-    p->tile_n = 0;
-    p->group_chunks = 0;
-  }
-  p->chunk_px = kChunkPx;
-}
-
-rsim_plan default_plan(int tier, const Consts& k, int64_t P, int num_sms) {
-  rsim_plan p{};
-  resolve_tile(tier, k, &p);
-  p.splits = default_splits(tier, k.V, k.Ns, k.L, p.tile_n, P, num_sms);
-  return p;
-}
-
-std::string plan_problem(int tier, const Consts& k, const rsim_plan& p) {
-  if (p.splits < 1 || p.splits > kMaxSplits) return "plan splits must be in 1..64";
-  if (p.grid < 0) return "plan grid must be >= 0";
-  if (p.variant != 0) return "plan variant must be 0";
-  if (tier == RSIM_TIER_FP32) {
-    if (p.tile_n != 0 && p.tile_n != 64 && p.tile_n != 128) return "FP32 tile_n must be 64 or 128";
-  } else if (tensor_tier(tier)) {
-    const int lmax = std::max(8, (k.L + 7) / 8 * 8);
-    if (p.tile_n != 0 && (p.tile_n < 8 || p.tile_n > 128 || p.tile_n % 8 != 0 || p.tile_n > lmax))
-      return "tensor-core tile_n must be a multiple of 8 in 8..min(128, L rounded up to 8)";
-    if (p.group_chunks < 0 || p.group_chunks > group_chunks_max(tier))
-      return "group_chunks must be in 1.." + std::to_string(group_chunks_max(tier)) + " for this tier";
-  }
-  return std::string();
 }
 
 }  // namespace rsim

@@ -706,62 +706,6 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   }
 }
 
-// cube = scale * sum over splits s = 0, 1, ... (in this order) of the tiled partial
-// sums, with compensated FP32 additions per component.  One thread per (accumulator
-// row, column pair) of a tile: the loads of consecutive threads are contiguous.  The
-// loads of kReduceBatch splits are issued together (a frame's splits in one or two round
-// trips to memory); the additions keep the split order.
-__global__ void split_reduce_tiles(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles,
-                                   int64_t sstride, int splits, int out_dtype, int scale_mode) {
-  wait_prior_grid();
-  const FrameIO& fr = frames[blockIdx.y];
-  float scale = 1.f;
-  if (scale_mode) {
-    const float m = __uint_as_float((unsigned)fr.meta[1]);
-    scale = (m > 0.f) ? ldexpf(1.f, ilogbf(m) + 1) : 1.f;
-  }
-  const int64_t rows = (int64_t)k.V * k.Ns;
-  const int64_t n4 = sstride / 2;
-  const int pairs = NT / 2;
-  const float4* __restrict__ part = reinterpret_cast<const float4*>(fr.partial);
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
-    const int r = (int)(e & 127);
-    const int64_t q = e >> 7;
-    const int pr = (int)(q % pairs);
-    const int64_t tile = q / pairs;
-    const int64_t row = (tile / ntiles) * 128 + r;
-    const int l = (int)(tile % ntiles) * NT + 2 * pr;
-    if (row >= rows || l >= k.L) continue;
-    float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-    for (int b = 0; b < splits; b += kReduceBatch) {
-      float4 p[kReduceBatch];
-#pragma unroll
-      for (int j = 0; j < kReduceBatch; ++j)
-        p[j] = (b + j < splits) ? __ldcs(part + (int64_t)(b + j) * n4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-      for (int j = 0; j < kReduceBatch; ++j) {
-        if (b + j < splits) {
-          kahan_add(s0, c0, p[j].x);
-          kahan_add(s1, c1, p[j].y);
-          kahan_add(s2, c2, p[j].z);
-          kahan_add(s3, c3, p[j].w);
-        }
-      }
-    }
-    const int64_t o = row * k.L + l;
-    const bool two = (l + 1 < k.L);
-    if (out_dtype == RSIM_C128) {
-      double2* cd = reinterpret_cast<double2*>(fr.cube);
-      cd[o] = make_double2((double)(s0 * scale), (double)(s1 * scale));
-      if (two) cd[o + 1] = make_double2((double)(s2 * scale), (double)(s3 * scale));
-    } else {
-      float2* cf = reinterpret_cast<float2*>(fr.cube);
-      cf[o] = make_float2(s0 * scale, s1 * scale);
-      if (two) cf[o + 1] = make_float2(s2 * scale, s3 * scale);
-    }
-  }
-}
-
 // Frames by decreasing valid-pixel count (ties by index): the persistent kernel takes
 // the units of the largest frames first.
 __global__ void order_frames(const FrameIO* __restrict__ frames, int F, int32_t* order) {
@@ -812,26 +756,6 @@ cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, in
 }
 
 }  // namespace
-
-int tile_nt(int L) { return L >= 128 ? 128 : ((L + 7) / 8) * 8; }
-
-int64_t tensor_split_stride(int V, int Ns, int L, int nt) {
-  const int64_t mtiles = ((int64_t)V * Ns + 127) / 128;
-  return mtiles * ((L + nt - 1) / nt) * 128 * nt;
-}
-
-cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int nt,
-                                int out_dtype, bool scale_from_meta, int num_sms, cudaStream_t st) {
-  const int64_t sstride = tensor_split_stride(k.V, k.Ns, k.L, nt);
-  const int64_t n4 = sstride / 2;
-  if (n4 <= 0 || F <= 0) return cudaSuccess;
-  // one wave of resident blocks (8 x 256 threads per SM) over all frames, grid-stride
-  int64_t blocks = (n4 + 255) / 256;
-  const int64_t wave = std::max<int64_t>(1, 8ll * num_sms / F);
-  if (blocks > wave) blocks = wave;
-  return launch_dependent(split_reduce_tiles, dim3((unsigned)blocks, F), dim3(256), 0, st, frames, k, nt,
-                          (k.L + nt - 1) / nt, sstride, splits, out_dtype, scale_from_meta ? 1 : 0);
-}
 
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
                         int out_dtype, int grid, int nt, int group, bool use_partial, int num_sms,

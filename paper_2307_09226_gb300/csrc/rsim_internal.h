@@ -15,7 +15,7 @@ constexpr int kChunkPx = 32;        // pixels per pipeline stage / K-chunk (64 r
 constexpr int kPrepTile = 256;      // pixels per block of the compaction kernels
 constexpr int kPrepThreads = 256;
 constexpr int kMaxSplits = 64;
-constexpr int kReduceBatch = 16;    // split partials a reduction thread loads at once
+constexpr int kReduceBatch = 8;     // split partials a reduction thread loads at once
 
 // Host-resolved constants of one radar configuration.  The per-pixel FP64 phase
 // increments are products of these with R, u and vel (Eq. 1 / Eq. 2):
@@ -234,8 +234,9 @@ int units_per_split(int tier, int V, int Ns, int L, int tile_n);
 // the length bounds the error; see k_umma.cu).
 int group_chunks(int tier);
 int group_chunks_max(int tier);
-// Default n tile of the FP32 direct sum.
+// Default n tile of the FP32 direct sum, and its l tile (fixed).
 constexpr int kDirectTileN = 128;
+constexpr int kDirectTileL = 64;
 // Whether a frame of P pixels goes through the split-partial buffer + reduction.
 bool uses_partial(int tier, int64_t P, int splits, int group);
 
