@@ -708,7 +708,7 @@ def run_serving(ctx, tune_budget_s=45.0, slots=None, schedule=None):
     cfg = synth.load_config(5)
     n_requests, n_warmup, pool = cfg["requests"], cfg["warmup_requests"], cfg["distinct_frames"]
     slots = cfg["slots"] if slots is None else slots
-    seed, age_ms = cfg["seed"], cfg["age_limit_ms"]
+    seed, age_ms, express = cfg["seed"], cfg["age_limit_ms"], cfg["express_slots"]
     reqs = synth.serving_requests(pool, seed=seed)
     frames = [synth.request_frame(r) for r in reqs]
     pxs = [device.upload(f) for f in frames]
@@ -741,9 +741,10 @@ def run_serving(ctx, tune_budget_s=45.0, slots=None, schedule=None):
     _abi.rsim_server_destroy(srv)
     rng = np.random.default_rng(seed + 1)
 
-    def run(load, policy):
+    def run(load, policy, n_express):
         rate = load / alone_s
-        srv = _abi.rsim_server_create(ctx.h, slots=slots, policy=policy, age_limit_ms=age_ms)
+        srv = _abi.rsim_server_create(ctx.h, slots=slots, policy=policy, age_limit_ms=age_ms,
+                                      express_slots=n_express)
         bad = 0
 
         def stream(n, first):
@@ -769,7 +770,8 @@ def run_serving(ctx, tune_budget_s=45.0, slots=None, schedule=None):
         st = _abi.rsim_server_stats_get(srv)
         _abi.rsim_server_destroy(srv)
         torch.cuda.synchronize()
-        return {"offered_load": load, "policy": policy, "rate_req_s": round(rate, 2), "requests": int(st.completed),
+        return {"offered_load": load, "policy": policy, "express_slots": n_express, "rate_req_s": round(rate, 2),
+                "requests": int(st.completed),
                 "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),
                 "max_ms": round(st.max_ms, 3), "p99_queue_ms": round(st.p99_queue_ms, 3),
                 "max_queue_ms": round(st.max_queue_ms, 3), "overtakes": int(st.overtakes),
@@ -779,8 +781,9 @@ def run_serving(ctx, tune_budget_s=45.0, slots=None, schedule=None):
 
     loads = cfg["offered_loads"]
     if schedule is None:
-        schedule = [(x, "first_fit") for x in loads] + [(loads[0], "shortest_first")]
-    runs = [run(x, pol) for x, pol in schedule]
+        schedule = ([(x, "first_fit", express) for x in loads] + [(loads[0], "shortest_first", express)] +
+                    [(loads[0], "first_fit", 0)])
+    runs = [run(*item) for item in schedule]
     head = dict(runs[0])
     head.update({"workload": cfg["workload"],
                  "warmup_requests": n_warmup, "distinct_frames": pool, "slots": slots, "age_limit_ms": age_ms,

@@ -440,8 +440,11 @@ rsim_status rsim_get_plan(rsim_ctx* ctx, const rsim_radar_params* params, int64_
  * oldest first among equals).  Either way a request may be passed over only until it has
  * waited age_limit_ms since its submission: from then on the oldest such request goes
  * next and nothing overtakes it, so no request starves.  A request whose estimated device
- * time is under 2 ms runs on the slot's high-priority stream, so its blocks start ahead
- * of long requests' pending blocks; the others run at low priority.  Results do not
+ * time is under 2 ms ("short") runs on the slot's high-priority stream, so its blocks
+ * start ahead of long requests' pending blocks; the others run at low priority.  Express
+ * slots (rsim_server_opts.express_slots), beyond the general ones, take short requests
+ * only, so a short request does not wait in the queue while long requests hold every
+ * general slot; a short request also goes to a free express slot first.  Results do not
  * depend on the policy or the priority.  Completion is detected by a host function after
  * the request's work; latency is measured from submit() to completion.
  * ---------------------------------------------------------------------------------- */
@@ -450,12 +453,14 @@ typedef struct rsim_server rsim_server;
 enum { RSIM_SERVE_FIRST_FIT = 0, RSIM_SERVE_SHORTEST_FIRST = 1 };
 
 typedef struct {
-  int32_t slots;             /* concurrent requests on the device (>= 1) */
+  int32_t slots;             /* general slots: concurrent requests of any size (1..64) */
   int32_t max_queue;         /* queued requests accepted before submit() refuses (BUDGET) */
   size_t hbm_budget_bytes;   /* bound on the sum of admitted workspaces (0 = no bound) */
   int32_t policy;            /* RSIM_SERVE_FIRST_FIT (0) or RSIM_SERVE_SHORTEST_FIRST */
   int32_t age_limit_ms;      /* a queued request may be overtaken until it has waited this
                                 long (0 selects 100 ms; < 0: never overtaken, strict FIFO) */
+  int32_t express_slots;     /* further slots for short requests only (0..64) */
+  int32_t reserved;
 } rsim_server_opts;
 
 typedef struct {

@@ -92,7 +92,8 @@ SERVE_POLICIES = {"first_fit": SERVE_FIRST_FIT, "shortest_first": SERVE_SHORTEST
 
 class rsim_server_opts(Structure):
     _fields_ = [("slots", c_int32), ("max_queue", c_int32), ("hbm_budget_bytes", c_size_t),
-                ("policy", c_int32), ("age_limit_ms", c_int32)]
+                ("policy", c_int32), ("age_limit_ms", c_int32), ("express_slots", c_int32),
+                ("reserved", c_int32)]
 
 
 class rsim_request(Structure):
@@ -394,10 +395,10 @@ def rsim_get_plan(ctx, radar, P: int, tier: int) -> rsim_plan:
 
 
 def rsim_server_create(ctx, slots=4, max_queue=4096, hbm_budget_bytes=0, policy="first_fit",
-                       age_limit_ms=0) -> c_void_p:
+                       age_limit_ms=0, express_slots=0) -> c_void_p:
     h = c_void_p()
     opts = rsim_server_opts(int(slots), int(max_queue), int(hbm_budget_bytes), SERVE_POLICIES[policy],
-                            int(age_limit_ms))
+                            int(age_limit_ms), int(express_slots), 0)
     check(load().rsim_server_create(ctx, ctypes.byref(opts), ctypes.byref(h)))
     return h
 

@@ -6,7 +6,9 @@
 // reserved: the oldest that fits (first fit), or the one with the least estimated device
 // time among those that fit (shortest first).  A request can be passed over only until
 // it has waited the age limit; after that it is next, whether or not it fits yet, so no
-// request starves.  A request whose estimated device time is short runs on the
+// request starves.  Express slots, beyond the general ones, take only short requests
+// (estimated device time under 2 ms), so these never wait in the queue behind long
+// requests that hold every general slot.  A request whose estimated device time is short runs on the
 // high-priority stream: when long requests' kernels hold the SMs, the block scheduler
 // starts its blocks as soon as any resources free up instead of after the long kernels'
 // remaining blocks.  (Measured on the mixed serving workload: p50 and p99 both lower than
@@ -154,15 +156,21 @@ void retire(rsim_server* s, int si) {
 
 // Position in the queue of the request to admit next, or -1 when none may start now.
 // The queue is in submission order, so its head is the oldest request: once the head has
-// waited the age limit (or the limit is negative: strict FIFO) only the head may start.
-long pick_next(rsim_server* s, Clock::time_point now) {
+// waited the age limit (or the limit is negative: strict FIFO) only the head may start on
+// a general slot.  For an express slot (short_only) only short requests qualify; an aged
+// long head keeps its claim on the budget (an express request must leave room for it),
+// and an aged short head goes first.
+long pick_next(rsim_server* s, Clock::time_point now, bool short_only) {
   const size_t budget = s->opts.hbm_budget_bytes;
-  auto fits = [&](const Req& r) { return !budget || s->reserved + r.bytes <= budget; };
   const Req& head = s->reqs[s->queue.front()];
-  if (s->opts.age_limit_ms < 0 || now - head.t_submit >= s->age_limit) return fits(head) ? 0 : -1;
+  const bool head_aged = s->opts.age_limit_ms < 0 || now - head.t_submit >= s->age_limit;
+  const size_t keep = (short_only && head_aged && head.prio != 0) ? head.bytes : 0;
+  auto fits = [&](const Req& r) { return !budget || s->reserved + r.bytes + keep <= budget; };
+  if (head_aged && (!short_only || head.prio == 0)) return fits(head) ? 0 : -1;
   long best = -1;
   for (size_t i = 0; i < s->queue.size(); ++i) {
     const Req& r = s->reqs[s->queue[i]];
+    if (short_only && r.prio != 0) continue;
     if (!fits(r)) continue;
     if (s->opts.policy == RSIM_SERVE_FIRST_FIT) return (long)i;
     if (best < 0 || r.est_ms < s->reqs[s->queue[best]].est_ms) best = (long)i;
@@ -170,18 +178,31 @@ long pick_next(rsim_server* s, Clock::time_point now) {
   return best;
 }
 
-// Try to start one queued request on a free slot.  Called with the lock held.
+// Try to start one queued request on a free slot.  Called with the lock held.  Slots
+// [0, slots) are general; the express slots after them take short requests only, and a
+// short request picked for a general slot goes to a free express slot instead, keeping
+// the general slots for long requests.
 bool admit_one(rsim_server* s) {
   if (s->queue.empty()) return false;
-  int free_slot = -1;
-  for (size_t i = 0; i < s->slots.size(); ++i)
-    if (!s->slots[i].busy) {
-      free_slot = (int)i;
-      break;
-    }
-  if (free_slot < 0) return false;
+  const int n_general = s->opts.slots;
+  int gen = -1, exp = -1;
+  for (int i = 0; i < (int)s->slots.size(); ++i) {
+    if (s->slots[i].busy) continue;
+    if (i < n_general && gen < 0) gen = i;
+    if (i >= n_general && exp < 0) exp = i;
+  }
+  if (gen < 0 && exp < 0) return false;
   const Clock::time_point now = Clock::now();
-  const long qi = pick_next(s, now);
+  long qi = -1;
+  int free_slot = -1;
+  if (gen >= 0) {
+    qi = pick_next(s, now, false);
+    if (qi >= 0) free_slot = (s->reqs[s->queue[qi]].prio == 0 && exp >= 0) ? exp : gen;
+  }
+  if (qi < 0 && exp >= 0) {
+    qi = pick_next(s, now, true);
+    free_slot = exp;
+  }
   if (qi < 0) return false;
   Req& r = s->reqs[s->queue[qi]];
   if (qi > 0) s->stats.overtakes++;
@@ -274,6 +295,8 @@ extern "C" {
 rsim_status rsim_server_create(rsim_ctx* ctx, const rsim_server_opts* opts, rsim_server** out) {
   if (!ctx || !opts || !out) return fail(RSIM_ERR_INVALID_ARG, "NULL argument");
   if (opts->slots < 1 || opts->slots > 64) return fail(RSIM_ERR_INVALID_ARG, "slots must be in 1..64");
+  if (opts->express_slots < 0 || opts->express_slots > 64)
+    return fail(RSIM_ERR_INVALID_ARG, "express_slots must be in 0..64");
   if (opts->max_queue < 1) return fail(RSIM_ERR_INVALID_ARG, "max_queue must be >= 1");
   if (opts->policy != RSIM_SERVE_FIRST_FIT && opts->policy != RSIM_SERVE_SHORTEST_FIRST)
     return fail(RSIM_ERR_INVALID_ARG, "unknown admission policy");
@@ -282,8 +305,9 @@ rsim_status rsim_server_create(rsim_ctx* ctx, const rsim_server_opts* opts, rsim
   s->ctx = ctx;
   s->opts = *opts;
   if (opts->age_limit_ms > 0) s->age_limit = std::chrono::milliseconds(opts->age_limit_ms);
-  s->slots.resize(opts->slots);
-  for (int i = 0; i < opts->slots; ++i) {
+  const int n_slots = opts->slots + opts->express_slots;
+  s->slots.resize(n_slots);
+  for (int i = 0; i < n_slots; ++i) {
     Slot& sl = s->slots[i];
     sl.index = i;
     int least = 0, greatest = 0;

@@ -57,7 +57,7 @@ def test_struct_layouts_match_header():
         assert _abi.PRIM_DTYPE.fields[name][1] == getattr(_abi.rsim_primitive, name).offset
     assert ctypes.sizeof(_abi.rsim_camera) == 8 + 4 * 8 + 8
     assert ctypes.sizeof(_abi.rsim_pixel_out) == ctypes.sizeof(_abi.rsim_pixels)
-    assert ctypes.sizeof(_abi.rsim_server_opts) == 24
+    assert ctypes.sizeof(_abi.rsim_server_opts) == 32
     assert ctypes.sizeof(_abi.rsim_request) == 80 + 64 + 8 + 8
     assert ctypes.sizeof(_abi.rsim_server_stats) == 4 * 8 + 6 * 8 + 8 + 8 + 3 * 8
 

@@ -187,6 +187,35 @@ def test_server_overtaking_and_age_limit(env, policy, age_ms, sleep_s, overtakes
         assert np.array_equal(cb.cpu().numpy(), ctx.synth(r, px, "fp32").cpu().numpy())
 
 
+def test_server_express_slot_serves_short_requests_first(env):
+    """With one general slot held by a long request and another long one queued, a short
+    request runs at once on the express slot (it overtakes the queued long one) and
+    finishes while the first long request is still running; every result equals the
+    request run alone."""
+    torch, _abi, device, ctx = env
+    big = Radar(M=4, N=12, Ns=512, L=256)
+    fa = synth.random_frame(big, 256, 256, seed=31, mask_frac=0.3)
+    fb = synth.random_frame(big, 256, 256, seed=32, mask_frac=0.3)
+    small = synth.parity_frame(seed=33, n_az=20, n_el=20)
+    pxs = [device.upload(fa), device.upload(fb), device.upload(small)]
+    radars = [big, big, small.radar]
+    cubes = [device.cube_tensor(r) for r in radars]
+    srv = _abi.rsim_server_create(ctx.h, slots=1, express_slots=1)
+    try:
+        ts = [_abi.rsim_server_submit(srv, _abi.make_request(r, px, _abi.TIER_FP32, cb))
+              for r, px, cb in zip(radars, pxs, cubes)]
+        assert _abi.rsim_server_wait(srv, ts[2], 30000) == _abi.OK
+        assert _abi.rsim_server_wait(srv, ts[0], 0) == _abi.ERR_TIMEOUT  # the long one still runs
+        for t in ts[:2]:
+            assert _abi.rsim_server_wait(srv, t, 60000) == _abi.OK
+        st = _abi.rsim_server_stats_get(srv)
+    finally:
+        _abi.rsim_server_destroy(srv)
+    assert st.completed == 3 and st.overtakes == 1
+    for r, px, cb in zip(radars, pxs, cubes):
+        assert np.array_equal(cb.cpu().numpy(), ctx.synth(r, px, "fp32").cpu().numpy())
+
+
 def test_server_cancel_and_errors(env):
     torch, _abi, device, ctx = env
     # one slot so that later requests stay queued behind a long first one
