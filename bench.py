@@ -741,9 +741,10 @@ def run_serving(ctx, tune_budget_s=45.0, slots=None, schedule=None):
     _abi.rsim_server_destroy(srv)
     rng = np.random.default_rng(seed + 1)
 
-    def run(load, policy, n_express):
+    def run(load, policy, n_express, n_general=None):
         rate = load / alone_s
-        srv = _abi.rsim_server_create(ctx.h, slots=slots, policy=policy, age_limit_ms=age_ms,
+        n_general = slots if n_general is None else n_general
+        srv = _abi.rsim_server_create(ctx.h, slots=n_general, policy=policy, age_limit_ms=age_ms,
                                       express_slots=n_express)
         bad = 0
 
@@ -770,7 +771,8 @@ def run_serving(ctx, tune_budget_s=45.0, slots=None, schedule=None):
         st = _abi.rsim_server_stats_get(srv)
         _abi.rsim_server_destroy(srv)
         torch.cuda.synchronize()
-        return {"offered_load": load, "policy": policy, "express_slots": n_express, "rate_req_s": round(rate, 2),
+        return {"offered_load": load, "policy": policy, "slots": n_general, "express_slots": n_express,
+                "rate_req_s": round(rate, 2),
                 "requests": int(st.completed),
                 "p50_ms": round(st.p50_ms, 3), "p99_ms": round(st.p99_ms, 3), "mean_ms": round(st.mean_ms, 3),
                 "max_ms": round(st.max_ms, 3), "p99_queue_ms": round(st.p99_queue_ms, 3),
@@ -781,12 +783,14 @@ def run_serving(ctx, tune_budget_s=45.0, slots=None, schedule=None):
 
     loads = cfg["offered_loads"]
     if schedule is None:
+        # the configured server at each load, shortest-first at the first load, and the same
+        # number of slots without express slots (all general) for comparison
         schedule = ([(x, "first_fit", express) for x in loads] + [(loads[0], "shortest_first", express)] +
-                    [(loads[0], "first_fit", 0)])
+                    [(loads[0], "first_fit", 0, slots + express)])
     runs = [run(*item) for item in schedule]
     head = dict(runs[0])
     head.update({"workload": cfg["workload"],
-                 "warmup_requests": n_warmup, "distinct_frames": pool, "slots": slots, "age_limit_ms": age_ms,
+                 "warmup_requests": n_warmup, "distinct_frames": pool, "age_limit_ms": age_ms,
                  "alone_mean_ms": round(alone_s * 1e3, 3),
                  "tuning": {"buckets": len(keys), "tuned": len(tuned), "requests_on_tuned_plans": on_tuned,
                             "pool": pool, "seconds": round(tune_s, 1)},

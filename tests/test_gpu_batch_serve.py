@@ -74,14 +74,15 @@ def _requests(n, seed=5):
     return reqs
 
 
-@pytest.mark.parametrize("policy", ["first_fit", "shortest_first"])
-def test_server_results_equal_alone(env, policy):
+@pytest.mark.parametrize("policy,slots,express", [("first_fit", 4, 0), ("shortest_first", 4, 0),
+                                                   ("first_fit", 3, 5)])
+def test_server_results_equal_alone(env, policy, slots, express):
     torch, _abi, device, ctx = env
     reqs = _requests(16)
     frames = [synth.request_frame(r) for r in reqs]
     pxs = [device.upload(f) for f in frames]
     cubes = [device.cube_tensor(f.radar) for f in frames]
-    srv = _abi.rsim_server_create(ctx.h, slots=4, policy=policy)
+    srv = _abi.rsim_server_create(ctx.h, slots=slots, policy=policy, express_slots=express)
     try:
         tickets = []
         for r, f, px, cb in zip(reqs, frames, pxs, cubes):
