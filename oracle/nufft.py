@@ -57,8 +57,8 @@ def es_transform(k, w, G, n_nodes=128):
 
 
 def grid_size(N):
-    """Smallest power of two >= 2 N (oversampling at least 2)."""
-    g = 1
+    """Smallest power of two >= 2 N (oversampling at least 2) and >= 16 cells."""
+    g = 16
     while g < 2 * N:
         g *= 2
     return g

@@ -225,6 +225,33 @@ def test_phase_cycles_matches_the_phase_written_out_term_by_term():
                     assert abs(cube[v, n, l] - z) < 1e-11 * max(1.0, abs(z))
 
 
+def test_path_terms_are_the_symbols_of_eq1_and_eq2():
+    """path_terms against the definitions written out per pixel with `math`: ascending
+    valid indices, complex strengths, the direction cosine, the per-channel path range
+    and the Doppler shift."""
+    rng = np.random.default_rng(17)
+    n = 9
+    R = rng.uniform(0.5, 9, n)
+    sr, si = rng.normal(size=n), rng.normal(size=n)
+    sr[[1, 6]] = 0.0
+    si[[1, 6]] = 0.0
+    si[4] = -0.0
+    sr[4] = 0.0   # -0 and +0: a miss
+    az, el, vel = rng.uniform(-1, 1, n), rng.uniform(-0.5, 0.5, n), rng.uniform(-3, 3, n)
+    radar = Radar(M=2, N=3, Ns=8, L=4)
+    r = radar.resolved()
+    t = oracle.path_terms(radar, Pixels(R, sr, si, az, el, vel))
+    valid = [p for p in range(n) if p not in (1, 4, 6)]
+    assert t["idx"].tolist() == valid
+    for q, p in enumerate(valid):
+        u = math.cos(el[p]) * math.sin(az[p])
+        assert t["sigma"][q] == complex(sr[p], si[p])
+        assert abs(t["u"][q] - u) < 1e-15
+        assert abs(t["fD"][q] - 2 * vel[p] / r.lam) < 1e-9
+        for v in range(6):
+            assert abs(t["R_pv"][v, q] - (R[p] + v * r.d_rx * u / 2)) < 1e-12
+
+
 def test_rel_l2_is_the_normwise_relative_error_over_the_whole_cube():
     """The yardstick of every parity claim, against values worked out by hand."""
     assert oracle.rel_l2(np.array([3 + 4j]), np.array([0j])) == 5.0  # zero reference: absolute

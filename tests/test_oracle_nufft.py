@@ -59,3 +59,9 @@ def test_empty_frame_is_zero():
     px.sigma_re[:] = 0.0
     px.sigma_im[:] = 0.0
     assert np.all(nu.cube_nufft(f.radar, px, w=7) == 0)
+
+
+def test_grid_size_is_the_oversampled_power_of_two():
+    """G = the smallest power of two >= 2 N, and at least 16 cells."""
+    assert [nu.grid_size(n) for n in (4, 7, 8, 9, 64, 65, 128, 129, 2048)] == \
+        [16, 16, 16, 32, 128, 256, 256, 512, 4096]
