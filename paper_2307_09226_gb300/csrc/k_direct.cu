@@ -37,12 +37,48 @@ __device__ __forceinline__ void cmac(float2& acc, float2 g, float2 d) {
   acc.y = fmaf(g.y, d.x, acc.y);
 }
 
-// Phasor tiles of one 32-pixel chunk: G[q][n] = e^{j 2 pi (a n + c)} (channel v),
-// D[q][l] = sigma e^{j 2 pi b l}; zero outside the frame / the cube.
+// The raw per-pixel data of one 32-pixel chunk (this channel's phases, the slow-time
+// increment and sigma), copied into shared memory asynchronously one chunk ahead of its
+// use, so that the phasor fill never waits for global memory.
+struct RawChunk {
+  uint32_t a[kChunkPx];
+  uint32_t c[kChunkPx];
+  uint32_t b[kChunkPx];
+  float2 sig[kChunkPx];
+};
+constexpr int kRawCopies = (int)sizeof(RawChunk) / 16;  // 16-byte copies per chunk (40)
+
+// Issue the copies of chunk q0 / 32 into `raw` (threads 0..kRawCopies-1, one 16-byte
+// cp.async each) and commit them as one group.  The sources are 16-byte aligned (rows
+// of kChunkPx words start at multiples of 128 bytes) and lie within the frame's
+// capacity, also for the last chunk.
+__device__ __forceinline__ void stage_raw(RawChunk* raw, const FrameIO& fr, const uint32_t* pA,
+                                          const uint32_t* pC, int64_t q0) {
+  const int t = threadIdx.x;
+  if (t < kRawCopies) {
+    const char* src;
+    if (t < 8)
+      src = reinterpret_cast<const char*>(pA + q0) + 16 * t;
+    else if (t < 16)
+      src = reinterpret_cast<const char*>(pC + q0) + 16 * (t - 8);
+    else if (t < 24)
+      src = reinterpret_cast<const char*>(fr.phB + q0) + 16 * (t - 16);
+    else
+      src = reinterpret_cast<const char*>(fr.sig + q0) + 16 * (t - 24);
+    const uint32_t dst = (uint32_t)__cvta_generic_to_shared(reinterpret_cast<char*>(raw) + 16 * t);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void wait_raw_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void wait_raw_but_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Phasor tiles of one 32-pixel chunk from its staged raw data: G[q][n] = e^{j 2 pi (a n + c)}
+// (channel v), D[q][l] = sigma e^{j 2 pi b l}; zero outside the frame / the cube.
 template <int TN>
-__device__ __forceinline__ void fill_chunk(float2 (*Gs)[TN], float2 (*Ds)[kTL], const FrameIO& fr,
-                                           const uint32_t* pA, const uint32_t* pC, int64_t q0,
-                                           int64_t pv, int n0, int l0, const Consts& k) {
+__device__ __forceinline__ void fill_chunk(float2 (*Gs)[TN], float2 (*Ds)[kTL], const RawChunk& raw,
+                                           int64_t q0, int64_t pv, int n0, int l0, const Consts& k) {
   const int tid = threadIdx.x;
 #pragma unroll
   for (int i = 0; i < (kChunkPx * TN) / kThreads; ++i) {
@@ -51,7 +87,7 @@ __device__ __forceinline__ void fill_chunk(float2 (*Gs)[TN], float2 (*Ds)[kTL], 
     const int64_t q = q0 + qq;
     const int n = n0 + nn;
     float2 g = make_float2(0.f, 0.f);
-    if (q < pv && n < k.Ns) g = cis_q32(pA[q] * (uint32_t)n + pC[q]);
+    if (q < pv && n < k.Ns) g = cis_q32(raw.a[qq] * (uint32_t)n + raw.c[qq]);
     Gs[qq][nn] = g;
   }
 #pragma unroll
@@ -62,8 +98,8 @@ __device__ __forceinline__ void fill_chunk(float2 (*Gs)[TN], float2 (*Ds)[kTL], 
     const int l = l0 + ll;
     float2 d = make_float2(0.f, 0.f);
     if (q < pv && l < k.L) {
-      const float2 w = cis_q32(fr.phB[q] * (uint32_t)l);
-      const float2 sg = fr.sig[q];
+      const float2 w = cis_q32(raw.b[qq] * (uint32_t)l);
+      const float2 sg = raw.sig[qq];
       d = make_float2(sg.x * w.x - sg.y * w.y, sg.x * w.y + sg.y * w.x);
     }
     Ds[qq][ll] = d;
@@ -71,8 +107,9 @@ __device__ __forceinline__ void fill_chunk(float2 (*Gs)[TN], float2 (*Ds)[kTL], 
 }
 
 // One CTA: a TN (n) x 64 (l) tile of one channel over one pixel split.  Each thread
-// owns MI = TN / 16 n x 4 l complex outputs; the phasor tiles are double-buffered so that
-// the next chunk is filled before the barrier that hands it over.
+// owns MI = TN / 16 n x 4 l complex outputs.  The phasor tiles are double-buffered, so
+// that the next chunk is filled before the barrier that hands it over, and the raw data
+// of the chunk after that is copied into shared memory meanwhile (cp.async).
 template <int TN>
 __global__ void __launch_bounds__(kThreads, 2)
 direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_per_frame,
@@ -96,10 +133,11 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
   const int64_t nch = (pv + kChunkPx - 1) / kChunkPx;
   const int64_t c0 = nch * s / splits, c1 = nch * (s + 1) / splits;
 
-  extern __shared__ float2 dsm[];  // 2 x (G [32][TN] + D [32][64])
+  extern __shared__ float2 dsm[];  // 2 x (G [32][TN] + D [32][64]), then 2 raw chunks
   constexpr int kBuf = kChunkPx * (TN + kTL);
   auto gbuf = [&](int b) { return reinterpret_cast<float2 (*)[TN]>(dsm + b * kBuf); };
   auto dbuf = [&](int b) { return reinterpret_cast<float2 (*)[kTL]>(dsm + b * kBuf + kChunkPx * TN); };
+  RawChunk* raw = reinterpret_cast<RawChunk*>(dsm + 2 * kBuf);
 
   const int tid = threadIdx.x;
   const int tn = tid >> 4, tl = tid & 15;  // rows tn*MI .. +MI-1 ; cols tl + 16 j
@@ -112,11 +150,24 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
   const uint32_t* pA = fr.phA + (int64_t)v * fr.Pcap;
   const uint32_t* pC = fr.phC + (int64_t)v * fr.Pcap;
 
-  if (c0 < c1) fill_chunk<TN>(gbuf(0), dbuf(0), fr, pA, pC, c0 * kChunkPx, pv, n0, l0, k);
+  // raw chunk c sits in raw[(c - c0) & 1]; it is copied two iterations before its fill
+  if (c0 < c1) {
+    stage_raw(&raw[0], fr, pA, pC, c0 * kChunkPx);
+    if (c0 + 1 < c1) stage_raw(&raw[1], fr, pA, pC, (c0 + 1) * kChunkPx);
+    if (c0 + 1 < c1)
+      wait_raw_but_one();
+    else
+      wait_raw_all();
+    __syncthreads();
+    fill_chunk<TN>(gbuf(0), dbuf(0), raw[0], c0 * kChunkPx, pv, n0, l0, k);
+    wait_raw_all();
+  }
   __syncthreads();
   for (int64_t c = c0; c < c1; ++c) {
     const int b = (int)((c - c0) & 1);
-    if (c + 1 < c1) fill_chunk<TN>(gbuf(b ^ 1), dbuf(b ^ 1), fr, pA, pC, (c + 1) * kChunkPx, pv, n0, l0, k);
+    // raw[b] held chunk c, whose fill finished before the last barrier: chunk c + 2 goes there
+    if (c + 2 < c1) stage_raw(&raw[b], fr, pA, pC, (c + 2) * kChunkPx);
+    if (c + 1 < c1) fill_chunk<TN>(gbuf(b ^ 1), dbuf(b ^ 1), raw[b ^ 1], (c + 1) * kChunkPx, pv, n0, l0, k);
     const float2 (*G)[TN] = gbuf(b);
     const float2 (*D)[kTL] = dbuf(b);
 #pragma unroll 2
@@ -135,6 +186,7 @@ direct_sum(const FrameIO* __restrict__ frames, Consts k, int splits, int units_p
 #pragma unroll
         for (int j = 0; j < 4; ++j) cmac(acc[i][j], g[i], d[j]);
     }
+    wait_raw_all();  // chunk c + 2's copies (issued by this thread) have landed
     __syncthreads();
   }
 
@@ -173,7 +225,7 @@ cudaError_t launch_direct_t(const Consts& k, const FrameIO* frames, int F, int s
   const int64_t blocks = upf * F;
   if (blocks <= 0) return cudaSuccess;
   if (blocks > 0x7fffffffll) return cudaErrorInvalidConfiguration;
-  const int smem = (int)sizeof(float2) * 2 * kChunkPx * (TN + kTL);
+  const int smem = (int)sizeof(float2) * 2 * kChunkPx * (TN + kTL) + 2 * (int)sizeof(RawChunk);
   cudaError_t e = cudaFuncSetAttribute(direct_sum<TN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   return launch_dependent(direct_sum<TN>, dim3((unsigned)blocks), dim3(kThreads), (size_t)smem, st, frames, k,
