@@ -307,6 +307,34 @@ def test_autotune_picks_tile_shapes_per_bucket(env, tier):
         c.close()
 
 
+def test_batch_runs_the_tuned_plan_of_its_largest_frame(env):
+    """A batch takes the plan of its largest frame's shape bucket: after tuning that bucket
+    (here pinned to a non-default tile and group length), every frame of an uneven batch
+    equals the same frame alone under the same plan, bit for bit, and meets the oracle."""
+    torch, _abi, device, ctx = env
+    from paper_2307_09226_gb300 import device as dev
+    c = dev.Context(0)
+    try:
+        radar = Radar(M=2, N=4, Ns=128, L=136)
+        frames = [synth.random_frame(radar, a, b, seed=70 + i, mask_frac=0.3)
+                  for i, (a, b) in enumerate([(80, 60), (60, 50), (80, 64)])]
+        P = max(f.P for f in frames)  # 5120: bucket 4097..8192
+        _abi.rsim_set_plan(c.h, radar, P, _abi.TIER_SPLIT_FP16, splits=3, tile_n=64, group_chunks=17)
+        assert _abi.rsim_get_plan(c.h, radar, 3000, _abi.TIER_SPLIT_FP16).tile_n != 64  # another bucket
+        pxs = [dev.upload(f) for f in frames]
+        cubes = c.synth_batch(radar, pxs, "split_fp16")
+        assert c.sync_status() == _abi.OK
+        for f, px, cb in zip(frames, pxs, cubes):
+            got = cb.cpu().numpy()
+            # alone, each frame's own bucket: pin the same plan there so the kernels match
+            _abi.rsim_set_plan(c.h, radar, f.P, _abi.TIER_SPLIT_FP16, splits=3, tile_n=64, group_chunks=17)
+            alone = c.synth(radar, px, "split_fp16").cpu().numpy()
+            assert np.array_equal(got, alone)
+            assert oracle.rel_l2(got, oracle.cube_separable(radar, f)) <= 2e-5
+    finally:
+        c.close()
+
+
 @pytest.mark.parametrize("tier", ["split_fp16", "split_bf16", "bf16"])
 @pytest.mark.parametrize("tile_n,group", [(8, 1), (16, 7), (64, 40), (128, 0), (24, 0)])
 def test_pinned_tile_shapes_pass_parity(env, tier, tile_n, group):
