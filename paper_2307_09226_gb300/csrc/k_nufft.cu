@@ -483,11 +483,15 @@ __global__ void __launch_bounds__(kSpreadThreads, kSpreadBlocksPerSm) nu_spread(
         const float qr = q.q.x * scale, qi = q.q.y * scale;
         // tap j sits at z = (s + j - d) 2 / W in kernel units
         const float zx0 = ((float)sx - dx) * k2w, zy0 = ((float)sy - dy) * k2w;
+        // the hardware exponential's few-ulp error sets an error floor near 1e-6, below the
+        // kernel's own error for w <= 7; the widest kernel (w = 8, chosen for accuracy)
+        // keeps the library functions
 #pragma unroll
         for (int j = 0; j < W; ++j) {
-          const float wx = es_kernel_fast(fmaf((float)j, k2w, zx0), beta);
+          const float zx = fmaf((float)j, k2w, zx0), zy = fmaf((float)j, k2w, zy0);
+          const float wx = W >= 8 ? es_kernel(zx, beta) : es_kernel_fast(zx, beta);
           s_ax[warp][j][lane] = make_float2(qr * wx, qi * wx);
-          s_wy[warp][j][lane] = es_kernel_fast(fmaf((float)j, k2w, zy0), beta);
+          s_wy[warp][j][lane] = W >= 8 ? es_kernel(zy, beta) : es_kernel_fast(zy, beta);
         }
         s_base[warp][lane] = lx * STRIDE + ly;
       }
