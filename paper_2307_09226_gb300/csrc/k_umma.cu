@@ -468,12 +468,85 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
     // ------- A producers + accumulator drain: thread = accumulator row, kAPx pixels -------
     // A entries of padded pixels and of rows past the cube need no masking: the B image
     // rows of padded pixels are zero, and rows past the cube are never written out.
+    // A finished group's drain waits until this warp has made its first stage of the next
+    // group (the stage's ring slot belongs to MMAs already issued, so nothing there waits
+    // on the drain): the MMAs of the next group then start on a ready stage as soon as the
+    // accumulator is read out, instead of waiting for A to be made after the drain.
     const int quarter = warp & 3, part = (warp >> 2) & 1, group = warp >> 3;
     const int r = quarter * 32 + lane;
     const uint32_t lane_base = (uint32_t)(quarter * 32) << 16;
     uint32_t kk = 0, pk = 0, gi = 0, ui = 0;
     long long u;
     bool alive = true;
+    // the group whose drain is pending
+    struct Pending {
+      const FrameIO* fr;
+      int64_t gr;
+      float oscale;
+      int l0, s, mt, nt;
+      bool row_ok, none, first, set;
+    };
+    Pending pend;
+    pend.set = false;
+    auto drain = [&](const Pending& d) -> bool {
+      if (!warp_wait(&sh->acc_full, gi & 1u, sh, status)) return false;
+      fence_after();
+      const FrameIO& dfr = *d.fr;
+      for (int jb = ((warp >> 2) & 3) * 8; jb < g.NT; jb += 8 * (kAWarps / 4)) {
+        uint32_t re[8], im[8];
+        if (!d.none) {
+          tmem_ld8(tmem + lane_base + jb, re);
+          tmem_ld8(tmem + lane_base + g.NT + jb, im);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        } else {
+#pragma unroll
+          for (int i = 0; i < 8; ++i) re[i] = im[i] = 0u;
+        }
+        if (!d.row_ok) continue;
+        if (g.direct) {
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            const int l = d.l0 + jb + i;
+            if (l >= k.L) break;
+            const float a0 = __uint_as_float(re[i]), b0 = __uint_as_float(im[i]);
+            const float a1 = __uint_as_float(re[i + 1]), b1 = __uint_as_float(im[i + 1]);
+            const bool two = (l + 1 < k.L);
+            const int64_t o = d.gr * k.L + l;
+            if (out_dtype == RSIM_C128) {
+              double2* cd = reinterpret_cast<double2*>(dfr.cube);
+              cd[o] = make_double2((double)a0 * d.oscale, (double)b0 * d.oscale);
+              if (two) cd[o + 1] = make_double2((double)a1 * d.oscale, (double)b1 * d.oscale);
+            } else {
+              float2* cf = reinterpret_cast<float2*>(dfr.cube);
+              cf[o] = make_float2(a0 * d.oscale, b0 * d.oscale);
+              if (two) cf[o + 1] = make_float2(a1 * d.oscale, b1 * d.oscale);
+            }
+          }
+        } else {
+          // tiled partial sums: column pair p of accumulator row r is float4 p * 128 + r of
+          // the tile, so the warp's 32 rows write 512 contiguous bytes.  Later groups are
+          // added with reductions: no load round trip, and one thread owns each address, so
+          // its additions land in program order (deterministic).  Columns past L (last
+          // column tile) land in the tile's padding and are never read.
+          float4* t4 = reinterpret_cast<float4*>(dfr.partial + (int64_t)d.s * g.sstride +
+                                                 ((int64_t)d.mt * g.ntiles + d.nt) * (128 * g.NT)) +
+                       (jb >> 1) * 128 + r;
+#pragma unroll
+          for (int i = 0; i < 8; i += 2) {
+            const float4 v4 = make_float4(__uint_as_float(re[i]), __uint_as_float(im[i]),
+                                          __uint_as_float(re[i + 1]), __uint_as_float(im[i + 1]));
+            if (d.first)
+              t4[(i >> 1) * 128] = v4;
+            else
+              atomicAdd(t4 + (i >> 1) * 128, v4);
+          }
+        }
+      }
+      fence_before();
+      mbar_arrive(&sh->acc_empty);
+      ++gi;
+      return true;
+    };
     while (alive && next_unit(sh, ui++, status, &u, true)) {
       const Unit x = decode(g, frames, k, u);
       const FrameIO& fr = frames[x.f];
@@ -529,70 +602,27 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           fence_before();
           mbar_arrive(&sh->full[st]);
+          // the previous group's drain, now that this group's first stage of ours is made
+          if (pend.set) {
+            if (!drain(pend)) {
+              alive = false;
+              break;
+            }
+            pend.set = false;
+          }
         }
         if (!alive) break;
-        // ---- drain this group's accumulator (round-to-nearest FP32 adds) ----
-        if (!warp_wait(&sh->acc_full, gi & 1u, sh, status)) {
-          alive = false;
-          break;
-        }
-        fence_after();
-        const bool none = (g1 <= g0), first = (g0 == x.c0);
-        for (int jb = ((warp >> 2) & 3) * 8; jb < g.NT; jb += 8 * (kAWarps / 4)) {
-          uint32_t re[8], im[8];
-          if (!none) {
-            tmem_ld8(tmem + lane_base + jb, re);
-            tmem_ld8(tmem + lane_base + g.NT + jb, im);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          } else {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) re[i] = im[i] = 0u;
-          }
-          if (!row_ok) continue;
-          if (g.direct) {
-#pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-              const int l = l0 + jb + i;
-              if (l >= k.L) break;
-              const float a0 = __uint_as_float(re[i]), b0 = __uint_as_float(im[i]);
-              const float a1 = __uint_as_float(re[i + 1]), b1 = __uint_as_float(im[i + 1]);
-              const bool two = (l + 1 < k.L);
-              const int64_t o = gr * k.L + l;
-              if (out_dtype == RSIM_C128) {
-                double2* cd = reinterpret_cast<double2*>(fr.cube);
-                cd[o] = make_double2((double)a0 * oscale, (double)b0 * oscale);
-                if (two) cd[o + 1] = make_double2((double)a1 * oscale, (double)b1 * oscale);
-              } else {
-                float2* cf = reinterpret_cast<float2*>(fr.cube);
-                cf[o] = make_float2(a0 * oscale, b0 * oscale);
-                if (two) cf[o + 1] = make_float2(a1 * oscale, b1 * oscale);
-              }
-            }
-          } else {
-            // tiled partial sums: column pair p of accumulator row r is float4 p * 128 + r of
-            // the tile, so the warp's 32 rows write 512 contiguous bytes.  Later groups are
-            // added with reductions: no load round trip, and one thread owns each address, so
-            // its additions land in program order (deterministic).  Columns past L (last
-            // column tile) land in the tile's padding and are never read.
-            float4* t4 = reinterpret_cast<float4*>(fr.partial + (int64_t)x.s * g.sstride +
-                                                   ((int64_t)x.mt * g.ntiles + x.nt) * (128 * g.NT)) +
-                         (jb >> 1) * 128 + r;
-#pragma unroll
-            for (int i = 0; i < 8; i += 2) {
-              const float4 v4 = make_float4(__uint_as_float(re[i]), __uint_as_float(im[i]),
-                                            __uint_as_float(re[i + 1]), __uint_as_float(im[i + 1]));
-              if (first)
-                t4[(i >> 1) * 128] = v4;
-              else
-                atomicAdd(t4 + (i >> 1) * 128, v4);
-            }
+        // a group in which this warp made no stage: the previous drain is due now
+        if (pend.set) {
+          if (!drain(pend)) {
+            alive = false;
+            break;
           }
         }
-        fence_before();
-        mbar_arrive(&sh->acc_empty);
-        ++gi;
+        pend = Pending{&fr, gr, oscale, l0, x.s, x.mt, x.nt, row_ok, g1 <= g0, g0 == x.c0, true};
       }
     }
+    if (alive && pend.set) drain(pend);  // the last group
   } else if (warp == kAWarps) {
     // ------------- MMA issuer (one thread) -------------
     if (lane == 0) {
