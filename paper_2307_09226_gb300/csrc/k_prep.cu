@@ -12,7 +12,11 @@
 // Two kernels, one grid row per frame:
 //   prep_count   - valid pixels per 256-pixel tile;
 //   prep_scatter - tile offset = sum of earlier tile counts, ordered in-tile rank by
-//                  warp ballots, then writes the index and the path phases.
+//                  warp ballots, then writes the index and the path phases.  For the
+//                  tensor-core tiers it writes only the slow-time phase and sigma: their
+//                  operand builder computes the fast-time and channel phases (the FP64
+//                  trigonometry) while it writes the slow-time operand images, so that
+//                  FP64 work runs beside memory-bound work instead of before it.
 // Both are deterministic (no atomics decide positions).
 #include <math.h>
 
@@ -26,34 +30,6 @@ namespace {
 template <typename T>
 __device__ __forceinline__ bool is_valid(const T* sre, const T* sim, int64_t p) {
   return (sre[p] != T(0)) || (sim[p] != T(0));
-}
-
-// frac(x) = x - floor(x) as an unsigned 64-bit fixed-point number of 2^-64 units, read
-// from the binary representation with integer operations (GB300's FP64 rate is a small
-// fraction of its integer rate).  x = m 2^(E - 1075) with the 53-bit significand m, so
-// frac(x) 2^64 = m 2^(E - 1011) mod 2^64: exact when that shift is >= 0, else rounded to
-// the nearest unit (half up).  A negative x gives 2^64 - frac(|x|) 2^64 (mod 2^64).
-__device__ __forceinline__ uint64_t frac_u64(double x) {
-  const uint64_t bits = (uint64_t)__double_as_longlong(x);
-  const int E = (int)((bits >> 52) & 0x7FF);
-  if (E == 0 || E == 0x7FF) return 0;  // zero, subnormal (< 2^-1022) or not finite
-  const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const int sh = E - 1011;
-  uint64_t f;
-  if (sh >= 64)
-    f = 0;  // x is a multiple of 2^64 units: an integer
-  else if (sh >= 0)
-    f = m << sh;
-  else if (sh >= -53)
-    f = (m >> -sh) + ((m >> (-sh - 1)) & 1ull);
-  else
-    f = 0;  // below half a unit
-  return (bits >> 63) ? (uint64_t)0 - f : f;
-}
-
-// Round a 2^-64 fixed-point fraction to the nearest 2^-32 unit (mod 1).
-__device__ __forceinline__ uint32_t top32(uint64_t x) {
-  return (uint32_t)((x + 0x80000000ull) >> 32);
 }
 
 // `one`: with use_one, the (single) frame's entry, passed by value and stored to
@@ -93,7 +69,7 @@ prep_count(FrameIO* __restrict__ frames, FrameIO one, int use_one, int* counter)
 
 template <typename T>
 __global__ void __launch_bounds__(kPrepThreads)
-prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigned* status) {
+prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, int defer, unsigned* status) {
   wait_prior_grid();
   const FrameIO& fr = frames[blockIdx.y];
   const int64_t base = (int64_t)blockIdx.x * kPrepTile;
@@ -160,25 +136,22 @@ prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigne
       if (!idx_only) {
         const double r = (double)f_r, a = (double)f_az, e = (double)f_el, w = (double)f_vel;
         double s_re = (double)f_re, s_im = (double)f_im;
-        const bool ok = isfinite(r) && r > 0.0 && isfinite(a) && isfinite(e) && isfinite(w) &&
-                        isfinite(s_re) && isfinite(s_im);
-        uint64_t A0 = 0, dA = 0, G = 0, Bq = 0, Bm = 0;
+        const bool ok = pixel_ok(r, a, e, w, s_re, s_im);
+        FastTerms t = {0, 0, 0, 0};
+        uint64_t Bq = 0;
         if (ok) {
-          const double u = cos(e) * sin(a);       // direction cosine
-          A0 = frac_u64(k.k_a0 * r);              // 2 mu R_p / (c F_s)
-          dA = frac_u64(k.k_da * u);              // mu d_rx u / (c F_s): per channel index
-          G = frac_u64(k.k_g * u);                // d_rx u / lambda: per channel index
-          Bq = frac_u64(k.k_b * w);               // -2 vel T_slow / lambda
-          Bm = frac_u64(k.k_m * w);               // -2 vel T_b / lambda per Tx slot (or 0)
+          Bq = frac_u64(k.k_b * w);  // -2 vel T_slow / lambda
+          if (!defer) t = fast_terms(k, r, a, e, w);
         } else {
           atomicOr(status, kStatusNonfinite);
           s_re = 0.0;
           s_im = 0.0;
         }
-        for (int ch = 0; ch < k.V; ++ch) {
-          const uint64_t vv = (uint64_t)ch;
-          fr.phA[(int64_t)ch * fr.Pcap + q] = top32(A0 + vv * dA);
-          fr.phC[(int64_t)ch * fr.Pcap + q] = top32(vv * G + (uint64_t)(ch / k.N) * Bm);
+        if (!defer) {
+          for (int ch = 0; ch < k.V; ++ch) {
+            fr.phA[(int64_t)ch * fr.Pcap + q] = chan_a(t, ch);
+            fr.phC[(int64_t)ch * fr.Pcap + q] = chan_c(t, ch, k.N);
+          }
         }
         fr.phB[q] = top32(Bq);
         const float fr_re = (float)s_re, fr_im = (float)s_im;
@@ -205,7 +178,8 @@ prep_scatter(const FrameIO* __restrict__ frames, Consts k, int idx_only, unsigne
 }  // namespace
 
 cudaError_t launch_prep(const Consts& k, FrameIO* frames, const FrameIO* one, int F, int64_t maxP,
-                        int dtype, bool idx_only, unsigned* status, int* counter, cudaStream_t st) {
+                        int dtype, bool idx_only, bool defer_fast_terms, unsigned* status, int* counter,
+                        cudaStream_t st) {
   if (F <= 0) return cudaSuccess;
   const int nblk = (int)std::max<int64_t>(1, (maxP + kPrepTile - 1) / kPrepTile);
   dim3 grid(nblk, F);
@@ -215,12 +189,12 @@ cudaError_t launch_prep(const Consts& k, FrameIO* frames, const FrameIO* one, in
     prep_count<double><<<grid, kPrepThreads, 0, st>>>(frames, arg, use_one, counter);
     if (maxP > 0)
       return launch_dependent(prep_scatter<double>, grid, dim3(kPrepThreads), 0, st, (const FrameIO*)frames, k,
-                              idx_only ? 1 : 0, status);
+                              idx_only ? 1 : 0, defer_fast_terms ? 1 : 0, status);
   } else {
     prep_count<float><<<grid, kPrepThreads, 0, st>>>(frames, arg, use_one, counter);
     if (maxP > 0)
       return launch_dependent(prep_scatter<float>, grid, dim3(kPrepThreads), 0, st, (const FrameIO*)frames, k,
-                              idx_only ? 1 : 0, status);
+                              idx_only ? 1 : 0, defer_fast_terms ? 1 : 0, status);
   }
   return cudaGetLastError();
 }

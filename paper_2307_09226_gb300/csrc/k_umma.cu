@@ -27,11 +27,13 @@
 //   warp 17     takes work units from a device counter and bulk-copies each chunk's
 //               phases of the tile's channels into a shared-memory ring;
 //   warp 18     bulk-copies each chunk's B images into the operand stages.
-// An operand stage (A in tensor memory, B in shared memory) has one "full" mbarrier,
-// completed by the producer group's arrivals and the B copy's bytes, and one "empty"
-// mbarrier, completed by a tcgen05.commit after the stage's MMAs: the MMA thread waits
-// once and commits once per stage.  Every wait is bounded in time and a timeout sets a
-// status bit instead of hanging.
+// A and B have rings of their own: four A stages in tensor memory (the columns the
+// accumulator leaves free) and three B stages in shared memory (what its 227 KB hold),
+// so a producer group has four MMA stages of time, not three, to make its next A stage.
+// Each slot of either ring has a "full" mbarrier (the producer group's arrivals, or the
+// B copy's bytes) and an "empty" mbarrier, completed by a tcgen05.commit after the MMAs
+// that read it.  Every wait is bounded in time and a timeout sets a status bit instead
+// of hanging.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -40,7 +42,8 @@
 namespace rsim {
 namespace {
 
-constexpr int kStages = 3;                 // operand stages: A in tensor memory (64 columns), B in shared memory (64 KB)
+constexpr int kStages = 3;                 // B operand stages in shared memory (64 KB each: hi + lo)
+constexpr int kAStages = 4;                // A operand stages in tensor memory (64 columns each: hi + lo)
 constexpr int kPixStages = 6;              // ring of staged per-chunk pixel phases
 constexpr int kUnitSlots = 4;              // ring of work-unit ids
 constexpr int kMaxCh = 8;                  // channels a row tile may span for staging
@@ -53,6 +56,7 @@ constexpr int kBBytes = kBRowsMax * 128;   // one 16-bit operand part of one sta
 constexpr int kStageBytes = 2 * kBBytes;   // hi + lo
 constexpr int kAccCols = 256;              // accumulator columns (N <= 256 FP32)
 constexpr int kTmemCols = 512;
+static_assert(kAccCols + kAStages * 64 <= kTmemCols, "accumulator and A stages fit in tensor memory");
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s per wait, then give up
 
 // Per-chunk fast-time/channel phases staged by the pixel loader (bulk copies).
@@ -62,8 +66,10 @@ struct PixStage {
 };
 
 struct Shared {
-  uint64_t full[kStages];    // the stage's A (producer arrivals) and B (bulk-copy bytes) are in place
-  uint64_t empty[kStages];   // the MMAs are done with the stage (it may be rewritten)
+  uint64_t a_full[kAStages];   // the A stage is in tensor memory (producer group arrivals)
+  uint64_t a_empty[kAStages];  // the MMAs are done with the A stage (it may be rewritten)
+  uint64_t b_full[kStages];    // the B stage is in shared memory (bulk-copy bytes)
+  uint64_t b_empty[kStages];   // the MMAs are done with the B stage
   uint64_t pix_full[kPixStages];
   uint64_t pix_empty[kPixStages];
   uint64_t unit_full[kUnitSlots];
@@ -361,16 +367,45 @@ __device__ __forceinline__ bool next_unit(Shared* sh, uint32_t ui, unsigned* sta
 //       row NT + lt = (Im D, Re D), with D = sigma e^{j 2 pi b l} (scaled for FP16),
 //       16-byte units placed at (unit ^ (row & 7)) as the 128-byte swizzle wants;
 //   lo: the same for the low parts of the split tiers.
+// With fast_dtype >= 0 (the compaction deferred them) the first F * ph_blocks blocks
+// write the fast-time and channel phases phA / phC instead, one valid pixel per thread
+// (read through the index list, pixel arrays of that dtype): their FP64 trigonometry
+// runs on the SMs beside the image blocks' memory-bound work.
 // ---------------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ FastTerms gather_fast_terms(const Consts& k, const FrameIO& fr, int64_t p) {
+  const double r = (double)((const T*)fr.range)[p], a = (double)((const T*)fr.az)[p];
+  const double e = (double)((const T*)fr.el)[p], w = (double)((const T*)fr.vel)[p];
+  const double sr = (double)((const T*)fr.sre)[p], si = (double)((const T*)fr.sim)[p];
+  FastTerms t = {0, 0, 0, 0};
+  if (pixel_ok(r, a, e, w, sr, si)) t = fast_terms(k, r, a, e, w);
+  return t;
+}
+
 template <int BF, int SPLIT>
 __global__ void __launch_bounds__(256)
 build_b_images(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles, int64_t nch, int F,
-               int scaled) {
+               int scaled, int fast_dtype, int ph_blocks) {
   wait_prior_grid();
+  const int nph = fast_dtype >= 0 ? F * ph_blocks : 0;
+  if ((int)blockIdx.x < nph) {
+    const FrameIO& fr = frames[blockIdx.x / ph_blocks];
+    const int64_t q = (int64_t)(blockIdx.x % ph_blocks) * blockDim.x + threadIdx.x;
+    if (q < (int64_t)fr.meta[0]) {
+      const int64_t p = fr.idx[q];
+      const FastTerms t =
+          fast_dtype == RSIM_F64 ? gather_fast_terms<double>(k, fr, p) : gather_fast_terms<float>(k, fr, p);
+      for (int ch = 0; ch < k.V; ++ch) {
+        fr.phA[(int64_t)ch * fr.Pcap + q] = chan_a(t, ch);
+        fr.phC[(int64_t)ch * fr.Pcap + q] = chan_c(t, ch, k.N);
+      }
+    }
+    return;
+  }
   const size_t part = (size_t)2 * NT * 128;
   const int64_t items = (int64_t)F * ntiles * nch;
   // one chunk image per block and pass, chunks of a column tile consecutive
-  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+  for (int64_t it = blockIdx.x - nph; it < items; it += gridDim.x - nph) {
     const int64_t c = it % nch;
     const int nt = (int)((it / nch) % ntiles);
     const FrameIO& fr = frames[it / (nch * ntiles)];
@@ -432,9 +467,13 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   const uint32_t part = (uint32_t)(2 * g.NT * 128);
 
   if (threadIdx.x == 0) {
+    for (int i = 0; i < kAStages; ++i) {
+      mbar_init(&sh->a_full[i], 32 * kAGroupWarps);  // the threads of one producer group
+      mbar_init(&sh->a_empty[i], 1);
+    }
     for (int i = 0; i < kStages; ++i) {
-      mbar_init(&sh->full[i], 32 * kAGroupWarps + 1);  // one producer group + the B loader
-      mbar_init(&sh->empty[i], 1);
+      mbar_init(&sh->b_full[i], 1);  // the B loader's arrival with the bytes expected
+      mbar_init(&sh->b_empty[i], 1);
     }
     for (int i = 0; i < kPixStages; ++i) {
       mbar_init(&sh->pix_full[i], 1);
@@ -565,10 +604,10 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         const int64_t g0 = group_begin(x, ngr, gk), g1 = group_begin(x, ngr, gk + 1);
         for (int64_t c = g0; c < g1; ++c, ++kk, ++pk) {
           if ((int)(kk & 1u) != group) continue;  // the other group makes this stage
-          const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
+          const uint32_t st = kk % kAStages, ph = (kk / kAStages) & 1u;
           const uint32_t ps = pk % kPixStages, pph = (pk / kPixStages) & 1u;
           if (!warp_wait(&sh->pix_full[ps], pph, sh, status) ||
-              !warp_wait(&sh->empty[st], ph ^ 1u, sh, status)) {
+              !warp_wait(&sh->a_empty[st], ph ^ 1u, sh, status)) {
             alive = false;
             break;
           }
@@ -601,7 +640,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           if (SPLIT) tmem_st16(col + 32, lo);
           asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
           fence_before();
-          mbar_arrive(&sh->full[st]);
+          mbar_arrive(&sh->a_full[st]);
           // the previous group's drain, now that this group's first stage of ours is made
           if (pend.set) {
             if (!drain(pend)) {
@@ -642,16 +681,19 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           fence_after();
           uint32_t accum = 0;
           for (int64_t c = g0; c < g1; ++c, ++kk) {
-            const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-            if (!mbar_wait_fast(&sh->full[st], ph, sh, status)) {
+            const uint32_t sa = kk % kAStages, pa = (kk / kAStages) & 1u;
+            const uint32_t sb = kk % kStages, pb = (kk / kStages) & 1u;
+            if (!mbar_wait_fast(&sh->a_full[sa], pa, sh, status) ||
+                !mbar_wait_fast(&sh->b_full[sb], pb, sh, status)) {
               alive = false;
               break;
             }
             fence_after();
-            mma_stage<SPLIT>(tmem, tmem + kAccCols + st * 64, desc0 + (uint64_t)(st * (kStageBytes >> 4)),
+            mma_stage<SPLIT>(tmem, tmem + kAccCols + sa * 64, desc0 + (uint64_t)(sb * (kStageBytes >> 4)),
                              idesc, accum);
             accum = 1;
-            mma_commit(&sh->empty[st]);
+            mma_commit(&sh->a_empty[sa]);
+            mma_commit(&sh->b_empty[sb]);
           }
           if (!alive) break;
           if (g1 > g0)
@@ -713,15 +755,15 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
         const FrameIO& fr = frames[x.f];
         for (int64_t c = x.c0; c < x.c1; ++c, ++kk) {
           const uint32_t st = kk % kStages, ph = (kk / kStages) & 1u;
-          if (!mbar_wait(&sh->empty[st], ph ^ 1u, sh, status)) {
+          if (!mbar_wait(&sh->b_empty[st], ph ^ 1u, sh, status)) {
             alive = false;
             break;
           }
           const unsigned char* src = fr.bimg + ((int64_t)x.nt * fr.bimg_nch + c) * 2 * part;
           unsigned char* dst = bstage + st * kStageBytes;
-          mbar_expect_tx(&sh->full[st], SPLIT ? 2 * part : part);
-          bulk_g2s(dst, src, part, &sh->full[st]);
-          if (SPLIT) bulk_g2s(dst + kBBytes, src + part, part, &sh->full[st]);
+          mbar_expect_tx(&sh->b_full[st], SPLIT ? 2 * part : part);
+          bulk_g2s(dst, src, part, &sh->b_full[st]);
+          if (SPLIT) bulk_g2s(dst + kBBytes, src + part, part, &sh->b_full[st]);
         }
       }
     }
@@ -752,15 +794,18 @@ __global__ void order_frames(const FrameIO* __restrict__ frames, int F, int32_t*
 
 template <int BF, int SPLIT>
 cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, int num_sms, int scaled,
-                     int out_dtype, int64_t nch_max, unsigned* status, int* counter, cudaStream_t st,
-                     cudaEvent_t mid) {
+                     int out_dtype, int64_t nch_max, int fast_dtype, unsigned* status, int* counter,
+                     cudaStream_t st, cudaEvent_t mid) {
   cudaError_t e;
   if (nch_max > 0) {
     // one wave of resident blocks (8 x 256 threads per SM), looping over the chunk images
     const int64_t items = (int64_t)g.F * g.ntiles * nch_max;
-    const int blocks = (int)std::min<int64_t>(items, 8ll * num_sms);
-    e = launch_dependent(build_b_images<BF, SPLIT>, dim3(blocks), dim3(256), 0, st, frames, k, g.NT, g.ntiles,
-                         nch_max, g.F, scaled);
+    // the phase blocks come first (one valid pixel per thread), then the image blocks
+    const int ph_blocks = fast_dtype >= 0 ? (int)((nch_max * kChunkPx + 255) / 256) : 0;
+    const int64_t blocks = std::min<int64_t>(items, 8ll * num_sms) + (int64_t)g.F * ph_blocks;
+    if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    e = launch_dependent(build_b_images<BF, SPLIT>, dim3((unsigned)blocks), dim3(256), 0, st, frames, k, g.NT,
+                         g.ntiles, nch_max, g.F, scaled, fast_dtype, ph_blocks);
     if (e != cudaSuccess) return e;
   }
   if (mid) cudaEventRecord(mid, st);
@@ -789,8 +834,8 @@ cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, in
 
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
                         int out_dtype, int grid, int nt, int group, bool use_partial, int num_sms,
-                        int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st,
-                        cudaEvent_t mid) {
+                        int64_t max_p, int fast_terms_dtype, unsigned* status, int* unit_counter,
+                        cudaStream_t st, cudaEvent_t mid) {
   // N = 2 NT must be a multiple of 16 in 16..256 (kind::f16 with M = 128), and a group
   // holds at least one chunk
   if (nt < 8 || nt > kBRowsMax / 2 || nt % 8 != 0 || group < 1) return cudaErrorInvalidValue;
@@ -821,15 +866,21 @@ cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int split
     if (e != cudaSuccess) return e;
   }
   const int64_t nch_max = (max_p + kChunkPx - 1) / kChunkPx;
+  if (fast_terms_dtype >= 0 && fast_terms_dtype != RSIM_F32 && fast_terms_dtype != RSIM_F64)
+    return cudaErrorInvalidValue;
   switch (tier) {
     case RSIM_TIER_BF16:
-      return launch_t<1, 0>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, status, unit_counter, st, mid);
+      return launch_t<1, 0>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, fast_terms_dtype, status, unit_counter, st,
+                          mid);
     case RSIM_TIER_SPLIT_BF16:
-      return launch_t<1, 1>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, status, unit_counter, st, mid);
+      return launch_t<1, 1>(k, frames, g, grid, num_sms, 0, out_dtype, nch_max, fast_terms_dtype, status, unit_counter, st,
+                          mid);
     case RSIM_TIER_SPLIT_FP16:
-      return launch_t<0, 1>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, status, unit_counter, st, mid);
+      return launch_t<0, 1>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, fast_terms_dtype, status, unit_counter, st,
+                          mid);
     case RSIM_TIER_FP16:
-      return launch_t<0, 0>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, status, unit_counter, st, mid);
+      return launch_t<0, 0>(k, frames, g, grid, num_sms, 1, out_dtype, nch_max, fast_terms_dtype, status, unit_counter, st,
+                          mid);
     default:
       return cudaErrorInvalidValue;
   }

@@ -294,9 +294,12 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     cudaEventRecord(ev[0], st);
   }
   cudaError_t e;
+  // the tensor tiers' operand builder computes the fast-time and channel phases
+  const bool defer = tensor_tier(tier);
   {
-    NvtxRange r("compaction + FP64 phases");
-    e = launch_prep(k, table, F == 1 ? host.data() : nullptr, F, mp, frames[0].dtype, false, status, counter, st);
+    NvtxRange r(defer ? "compaction + slow-time phases" : "compaction + FP64 phases");
+    e = launch_prep(k, table, F == 1 ? host.data() : nullptr, F, mp, frames[0].dtype, false, defer, status,
+                    counter, st);
   }
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (prof) cudaEventRecord(ev[1], st);
@@ -363,7 +366,7 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   } else {
     NvtxRange r("operand images + tcgen05 contraction + split reduction");
     e = launch_umma(k, table, F, splits, tier, out_dtype, plan.grid, plan.tile_n, plan.group_chunks,
-                    use_partial, ctx->num_sms, mp, status, counter, st, prof ? ev[4] : nullptr);
+                    use_partial, ctx->num_sms, mp, frames[0].dtype, status, counter, st, prof ? ev[4] : nullptr);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     if (prof) cudaEventRecord(ev[2], st);
@@ -632,7 +635,7 @@ rsim_status rsim_valid_indices(rsim_ctx* ctx, const rsim_pixels* pixels, int32_t
   host[0].idx = idx;
   cudaError_t e = cudaMemcpyAsync(table, host.data(), sizeof(FrameIO), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
-  e = launch_prep(k, table, host.data(), 1, P, pixels->dtype, true, ctx->status_dev, nullptr, st);
+  e = launch_prep(k, table, host.data(), 1, P, pixels->dtype, true, false, ctx->status_dev, nullptr, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   e = cudaMemcpyAsync(p_valid, host[0].meta, 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "copy of the valid count");
@@ -669,7 +672,7 @@ rsim_status rsim_path_phases(rsim_ctx* ctx, const rsim_radar_params* params,
   host[0].Pcap = P;
   cudaError_t e = cudaMemcpyAsync(table, host.data(), sizeof(FrameIO), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "upload of the frame table");
-  e = launch_prep(k, table, host.data(), 1, P, pixels->dtype, false, ctx->status_dev, nullptr, st);
+  e = launch_prep(k, table, host.data(), 1, P, pixels->dtype, false, false, ctx->status_dev, nullptr, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   e = cudaMemcpyAsync(p_valid, host[0].meta, 8, cudaMemcpyDeviceToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "copy of the valid count");

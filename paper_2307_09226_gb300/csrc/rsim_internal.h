@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
@@ -196,6 +197,67 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
   c = (t - s) - y;
   s = t;
 }
+// frac(x) = x - floor(x) as an unsigned 64-bit fixed-point number of 2^-64 units, read
+// from the binary representation with integer operations (GB300's FP64 rate is a small
+// fraction of its integer rate).  x = m 2^(E - 1075) with the 53-bit significand m, so
+// frac(x) 2^64 = m 2^(E - 1011) mod 2^64: exact when that shift is >= 0, else rounded to
+// the nearest unit (half up).  A negative x gives 2^64 - frac(|x|) 2^64 (mod 2^64).
+__device__ __forceinline__ uint64_t frac_u64(double x) {
+  const uint64_t bits = (uint64_t)__double_as_longlong(x);
+  const int E = (int)((bits >> 52) & 0x7FF);
+  if (E == 0 || E == 0x7FF) return 0;  // zero, subnormal (< 2^-1022) or not finite
+  const uint64_t m = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = E - 1011;
+  uint64_t f;
+  if (sh >= 64)
+    f = 0;  // x is a multiple of 2^64 units: an integer
+  else if (sh >= 0)
+    f = m << sh;
+  else if (sh >= -53)
+    f = (m >> -sh) + ((m >> (-sh - 1)) & 1ull);
+  else
+    f = 0;  // below half a unit
+  return (bits >> 63) ? (uint64_t)0 - f : f;
+}
+
+// Round a 2^-64 fixed-point fraction to the nearest 2^-32 unit (mod 1).
+__device__ __forceinline__ uint32_t top32(uint64_t x) {
+  return (uint32_t)((x + 0x80000000ull) >> 32);
+}
+
+// A pixel whose fields are all finite and whose range is positive gets its path terms;
+// any other gets zero terms and zero strength, and the kernel that reads it reports it.
+__device__ __forceinline__ bool pixel_ok(double r, double a, double e, double w, double s_re, double s_im) {
+  return isfinite(r) && r > 0.0 && isfinite(a) && isfinite(e) && isfinite(w) && isfinite(s_re) &&
+         isfinite(s_im);
+}
+
+// The fast-time and channel terms of one pixel (Eq. 1 / Eq. 2, see Consts) in 2^-64-cycle
+// units, from FP64 arithmetic: A0 = 2 mu R / (c F_s), dA = mu d_rx u / (c F_s) and
+// G = d_rx u / lambda per channel index, Bm = -2 vel T_b / lambda per Tx slot (0 unless
+// the TDM motion term is on), with the direction cosine u = cos(el) sin(az).  The
+// compaction kernel and the tensor tiers' operand builder both call this, so the two
+// write the same bits.
+struct FastTerms {
+  uint64_t A0, dA, G, Bm;
+};
+__device__ __forceinline__ FastTerms fast_terms(const Consts& k, double r, double az, double el, double w) {
+  const double u = cos(el) * sin(az);
+  FastTerms t;
+  t.A0 = frac_u64(k.k_a0 * r);
+  t.dA = frac_u64(k.k_da * u);
+  t.G = frac_u64(k.k_g * u);
+  t.Bm = frac_u64(k.k_m * w);
+  return t;
+}
+// Channel ch's fast-time increment a_{p,ch} and spatial phase c_{p,ch}, in 2^-32 cycle.
+__device__ __forceinline__ uint32_t chan_a(const FastTerms& t, int ch) {
+  return top32(t.A0 + (uint64_t)ch * t.dA);
+}
+__device__ __forceinline__ uint32_t chan_c(const FastTerms& t, int ch, int N) {
+  return top32((uint64_t)ch * t.G + (uint64_t)(ch / N) * t.Bm);
+}
+
 // Bytes of one 16-bit part of one chunk's slow-time operand image (2 NT rows of 128 B).
 inline size_t bimg_part_bytes(int nt) { return (size_t)2 * nt * 128; }
 
@@ -203,8 +265,11 @@ inline size_t bimg_part_bytes(int nt) { return (size_t)2 * nt * 128; }
 // Compaction and phases.  `one` (F == 1 only, else NULL): the frame's entry, which the
 // first kernel stores to frames[0] (no upload needed); the kernels also clear each
 // frame's meta words and, when `counter` is given, the contraction's work-unit counter.
+// defer_fast_terms: write only the index, the slow-time phase and sigma; the fast-time and
+// channel phases (phA, phC) are left to the tensor tiers' operand builder.
 cudaError_t launch_prep(const Consts& k, FrameIO* frames, const FrameIO* one, int F, int64_t maxP,
-                        int dtype, bool write_idx_only, unsigned* status, int* counter, cudaStream_t st);
+                        int dtype, bool write_idx_only, bool defer_fast_terms, unsigned* status, int* counter,
+                        cudaStream_t st);
 // tile_n: n values per CTA tile (64 or 128).
 cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits, int tile_n,
                           int out_dtype, cudaStream_t st);
@@ -214,12 +279,14 @@ cudaError_t launch_reduce(const Consts& k, const FrameIO* frames, int F, int spl
 cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, int splits, int nt,
                                 int out_dtype, bool scale_from_meta, int num_sms, cudaStream_t st);
 // nt: column tile (l values, multiple of 8 in 8..128); group: chunks per accumulation
-// group.  mid: an event recorded between the operand builder and the contraction
-// kernel (profiling), or NULL.
+// group.  fast_terms_dtype: RSIM_F32 / RSIM_F64 when the operand builder is to write the
+// fast-time and channel phases (launch_prep deferred them; the pixels' dtype), or -1.
+// mid: an event recorded between the operand builder and the contraction kernel
+// (profiling), or NULL.
 cudaError_t launch_umma(const Consts& k, const FrameIO* frames, int F, int splits, int tier,
                         int out_dtype, int grid, int nt, int group, bool use_partial, int num_sms,
-                        int64_t max_p, unsigned* status, int* unit_counter, cudaStream_t st,
-                        cudaEvent_t mid = nullptr);
+                        int64_t max_p, int fast_terms_dtype, unsigned* status, int* unit_counter,
+                        cudaStream_t st, cudaEvent_t mid = nullptr);
 
 cudaError_t launch_range_doppler(const float2* const* cubes_dev, float2* tmp, float* power, int F,
                                  int V, int Ns, int L, int skip_static, double v_per_bin, float* v_est,

@@ -125,7 +125,8 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   if (!device_status) e = cudaMemsetAsync(status, 0, 4, st);
   if (e != cudaSuccess) return cuda_fail(e, "static workspace set-up");
 
-  e = launch_prep(k, table, &io, 1, P, pixels->dtype, false, status, counter, st);
+  const bool defer = tensor_tier(tier);  // the operand builder computes the fast-time phases
+  e = launch_prep(k, table, &io, 1, P, pixels->dtype, false, defer, status, counter, st);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (tier == RSIM_TIER_FP32) {
     e = launch_direct(k, table, 1, splits, plan.tile_n, out_dtype, st);
@@ -133,7 +134,7 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
     if (use_partial) e = launch_reduce(k, table, 1, splits, out_dtype, 0.f, st);
   } else {
     e = launch_umma(k, table, 1, splits, tier, out_dtype, 0, plan.tile_n, plan.group_chunks, use_partial, sms,
-                    P, status, counter, st);
+                    P, pixels->dtype, status, counter, st);
     if (e == cudaErrorNotSupported) return fail(RSIM_ERR_UNSUPPORTED, "tensor-core tier not available");
     if (e != cudaSuccess) return cuda_fail(e, "tcgen05 contraction kernel");
     const bool scaled = (tier == RSIM_TIER_SPLIT_FP16 || tier == RSIM_TIER_FP16);
