@@ -144,6 +144,42 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
                : "memory");
 }
 
+// L2 eviction priorities.  A chunk's B images are read by every row tile at about the
+// same time and then never again, while the split partial sums wait in L2 for the
+// reduction after the contraction: the B copies take evict_first and the partial-sum
+// stores and reductions evict_last, so the streaming images do not push the partials out.
+// bulk_g2s with a createpolicy policy for the source lines:
+__device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                              uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+// 16-byte store and FP32 add-reduction with a policy (the reduction is one instruction,
+// like atomicAdd on a float4, so each address's additions keep the issuing thread's order).
+__device__ __forceinline__ void st_hint_v4(float4* a, float4 v, uint64_t policy) {
+  asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w), "l"(policy)
+               : "memory");
+}
+__device__ __forceinline__ void red_hint_v4(float4* a, float4 v, uint64_t policy) {
+  asm volatile("red.global.add.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(a), "f"(v.x), "f"(v.y),
+               "f"(v.z), "f"(v.w), "l"(policy)
+               : "memory");
+}
+
 // 1-D bulk copy global -> shared (16-byte aligned, size a multiple of 16) that
 // completes `bytes` of the barrier's transaction count.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -383,7 +419,7 @@ __device__ __forceinline__ FastTerms gather_fast_terms(const Consts& k, const Fr
 }
 
 template <int BF, int SPLIT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 6)
 build_b_images(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles, int64_t nch, int F,
                int scaled, int fast_dtype, int ph_blocks) {
   wait_prior_grid();
@@ -415,30 +451,36 @@ build_b_images(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles,
     unsigned char* base = fr.bimg + ((int64_t)nt * fr.bimg_nch + c) * 2 * part;
     const int64_t q0c = c * kChunkPx;
     // element (l, 16-byte column cp): four pixels' D at l, written to the re-row l and
-    // the im-row NT + l, which share a swizzle pattern (NT is a multiple of 8)
+    // the im-row NT + l, which share a swizzle pattern (NT is a multiple of 8).  A thread's
+    // elements e, e + 256, ... keep cp = e & 7 and row & 7, so they share the four pixels
+    // qg = cp ^ (row & 7): their phases and strengths are loaded once.
+    const int cp = threadIdx.x & 7;
+    const int qg = cp ^ ((threadIdx.x >> 3) & 7);
+    const int64_t q0 = q0c + qg * 4;
+    const uint4 b4 = *reinterpret_cast<const uint4*>(fr.phB + q0);
+    const float4 s01 = *reinterpret_cast<const float4*>(fr.sig + q0);
+    const float4 s23 = *reinterpret_cast<const float4*>(fr.sig + q0 + 2);
+    const uint32_t bv[4] = {b4.x, b4.y, b4.z, b4.w};
+    const float sa[4] = {s01.x * sc, s01.z * sc, s23.x * sc, s23.z * sc};
+    const float sb[4] = {s01.y * sc, s01.w * sc, s23.y * sc, s23.w * sc};
     for (int e = threadIdx.x; e < NT * 8; e += blockDim.x) {
-      const int row = e >> 3, cp = e & 7;
-      const int qg = cp ^ (row & 7);
+      const int row = e >> 3;
       const int l = nt * NT + row;
-      const int64_t q0 = q0c + qg * 4;
-      const uint4 b4 = *reinterpret_cast<const uint4*>(fr.phB + q0);
-      const float4 s01 = *reinterpret_cast<const float4*>(fr.sig + q0);
-      const float4 s23 = *reinterpret_cast<const float4*>(fr.sig + q0 + 2);
-      const uint32_t bv[4] = {b4.x, b4.y, b4.z, b4.w};
-      const float sr[4] = {s01.x, s01.z, s23.x, s23.z};
-      const float si[4] = {s01.y, s01.w, s23.y, s23.w};
       uint32_t rhi[4], rlo[4], ihi[4], ilo[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         float dre = 0.f, dim = 0.f;
         if (l < k.L && q0 + i < pv) {
           const float2 w = cis_q32(bv[i] * (uint32_t)l);
-          const float a = sr[i] * sc, b = si[i] * sc;
-          dre = a * w.x - b * w.y;
-          dim = a * w.y + b * w.x;
+          dre = sa[i] * w.x - sb[i] * w.y;
+          dim = sa[i] * w.y + sb[i] * w.x;
         }
         split2<BF>(dre, -dim, rhi[i], rlo[i]);
-        split2<BF>(dim, dre, ihi[i], ilo[i]);
+        // the im-row pair (dim, dre): the re-row pair (dre, -dim) with its 16-bit halves
+        // swapped and the new low half negated (rounding to nearest is odd, so these are
+        // the values a second split would give; only a zero may change sign)
+        ihi[i] = __byte_perm(rhi[i], 0, 0x1032) ^ 0x8000u;
+        ilo[i] = __byte_perm(rlo[i], 0, 0x1032) ^ 0x8000u;
       }
       const size_t off = (size_t)row * 128 + cp * 16, ioff = off + (size_t)NT * 128;
       *reinterpret_cast<uint4*>(base + off) = make_uint4(rhi[0], rhi[1], rhi[2], rhi[3]);
@@ -527,6 +569,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
     };
     Pending pend;
     pend.set = false;
+    const uint64_t pol_p = policy_evict_last();
     auto drain = [&](const Pending& d) -> bool {
       if (!warp_wait(&sh->acc_full, gi & 1u, sh, status)) return false;
       fence_after();
@@ -575,9 +618,9 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
             const float4 v4 = make_float4(__uint_as_float(re[i]), __uint_as_float(im[i]),
                                           __uint_as_float(re[i + 1]), __uint_as_float(im[i + 1]));
             if (d.first)
-              t4[(i >> 1) * 128] = v4;
+              st_hint_v4(t4 + (i >> 1) * 128, v4, pol_p);
             else
-              atomicAdd(t4 + (i >> 1) * 128, v4);
+              red_hint_v4(t4 + (i >> 1) * 128, v4, pol_p);
           }
         }
       }
@@ -747,6 +790,7 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
   } else {
     // ------------- B loader: bulk copies of the chunk's B images into the operand stage -------------
     if (lane == 0) {
+      const uint64_t pol_b = policy_evict_first();
       uint32_t kk = 0, ui = 0;
       long long u;
       bool alive = true;
@@ -762,8 +806,8 @@ umma_contract(const FrameIO* __restrict__ frames, Consts k, Geo g, int scaled, i
           const unsigned char* src = fr.bimg + ((int64_t)x.nt * fr.bimg_nch + c) * 2 * part;
           unsigned char* dst = bstage + st * kStageBytes;
           mbar_expect_tx(&sh->b_full[st], SPLIT ? 2 * part : part);
-          bulk_g2s(dst, src, part, &sh->b_full[st]);
-          if (SPLIT) bulk_g2s(dst + kBBytes, src + part, part, &sh->b_full[st]);
+          bulk_g2s_hint(dst, src, part, &sh->b_full[st], pol_b);
+          if (SPLIT) bulk_g2s_hint(dst + kBBytes, src + part, part, &sh->b_full[st], pol_b);
         }
       }
     }
