@@ -398,6 +398,13 @@ def run_gpu(args):
         traffic = _load_traffic(tier)
         if traffic is not None:
             roof["traffic"] = traffic
+        if roof.get("kernel") == "umma_contract":
+            # the device's measured rate on the contraction's own MMA instruction: the
+            # ceiling of the executed rate (the cuBLAS peak above also spends time outside
+            # its MMAs, so a kernel can execute above it)
+            mma = _abi.rsim_measure_mma_rate(ctx.h) / 1e12
+            roof["mma_rate_tflops"] = round(mma, 1)
+            roof["executed_frac_of_mma_rate"] = round(roof["executed_tflops"] / mma, 4)
         one_v, one_sample, _ = _cpu_one_core(frame)
         batch = run_batch(ctx, tier, steps=max(3, min(args.steps, 10)), warmup=3) if not args.no_extras else None
         serving = run_serving(ctx) if not args.no_extras else None

@@ -352,6 +352,18 @@ rsim_status rsim_selftest_wait_timeout(rsim_ctx* ctx, uint64_t limit_ns, rsim_st
  * Errors: INVALID_ARG, CUDA. */
 rsim_status rsim_measure_smem_atomics(rsim_ctx* ctx, double* lane_ops_per_s, rsim_stream stream);
 
+/* Measurement helper for benchmarks (no counterpart in the paper): the flop rate of this
+ * device's tensor cores on the contraction's instruction, tcgen05.mma kind::f16 with
+ * M = 128, N = 256, K = 16, A from tensor memory, B from shared memory and FP32
+ * accumulation, issued in the contraction's stages of 12 MMAs (one thread per CTA, at
+ * most three committed stages in flight, one CTA per SM, zero operands).  It is the
+ * ceiling of the contraction's executed flop rate.  Runs the probe six times on `stream`
+ * (the first as a warm-up) and returns the best, in flop/s (2 per multiply-add);
+ * synchronous.  Allocates nothing; every wait in the probe is bounded.
+ * Errors: INVALID_ARG, UNSUPPORTED (not an sm_103 device), TIMEOUT (a probe wait ran
+ * out), CUDA. */
+rsim_status rsim_measure_mma_rate(rsim_ctx* ctx, double* flops_per_s, rsim_stream stream);
+
 /* Stage timing for benchmarks.  While profiling is on, every rsim_synth /
  * rsim_synth_batch call records CUDA events on its stream around its three stages
  * (compaction + FP64 phases, contraction, split reduction), and around the main kernel

@@ -140,6 +140,7 @@ SIGNATURES = {
     "rsim_sync_status": (c_int, [c_void_p, c_void_p]),
     "rsim_selftest_wait_timeout": (c_int, [c_void_p, c_uint64, c_void_p]),
     "rsim_measure_smem_atomics": (c_int, [c_void_p, POINTER(c_double), c_void_p]),
+    "rsim_measure_mma_rate": (c_int, [c_void_p, POINTER(c_double), c_void_p]),
     "rsim_autotune": (c_int, [c_void_p, POINTER(rsim_radar_params), c_int64, c_int,
                               POINTER(rsim_plan), c_void_p]),
     "rsim_raycast": (c_int, [c_void_p, POINTER(rsim_camera), POINTER(rsim_primitive), c_int32,
@@ -371,6 +372,13 @@ def rsim_measure_smem_atomics(ctx, stream=None) -> float:
     """Measured shared-memory atomic rate of the device (lane operations per second)."""
     v = c_double()
     check(load().rsim_measure_smem_atomics(ctx, ctypes.byref(v), _stream(stream)))
+    return v.value
+
+
+def rsim_measure_mma_rate(ctx, stream=None) -> float:
+    """Measured flop rate of the contraction's tensor-core instruction on the device."""
+    v = c_double()
+    check(load().rsim_measure_mma_rate(ctx, ctypes.byref(v), _stream(stream)))
     return v.value
 
 

@@ -276,3 +276,14 @@ def test_tdm_motion_flag(ctx, tier):
     assert oracle.rel_l2(got, ref) <= TOL[tier]
     plain = oracle.cube_separable(f.radar, f.pixels)
     assert oracle.rel_l2(got, plain) > 1e-3  # the term is really there
+
+
+def test_tensor_core_rate_probe(ctx):
+    """The measured flop rate of the contraction's MMA instruction (the ceiling of its
+    executed rate) is plausible for this GPU: above 1 PFLOP/s and at most the rate of one
+    M=128, N=256, K=16 MMA per 128 clocks per SM at a 2.1 GHz clock on 152 SMs, with
+    headroom."""
+    from paper_2307_09226_gb300 import _abi
+    rate = _abi.rsim_measure_mma_rate(ctx.h)
+    print(f"tensor-core MMA rate: {rate / 1e12:.1f} TFLOP/s")
+    assert 1e15 < rate < 1.1 * 152 * (2 * 128 * 256 * 16 / 128) * 2.1e9
