@@ -117,6 +117,45 @@ def test_server_results_equal_alone(env, policy, slots, express):
         assert err <= TOL[reqs[i]["tier"]]
 
 
+def test_server_config5_stream_sampled_against_oracle(env):
+    """The serving workload's own request mix (all radar shapes up to 512 x 512 pixels,
+    FP32 and split-BF16), submitted at seeded exponential intervals so that requests
+    overlap on the device: every request completes, and a seeded 5% sample is checked
+    against the FP64 oracle at 32 random cube entries each (each entry its own FP64 sum
+    over the pixels), normwise over the sampled entries at the tier's tolerance."""
+    import time
+    torch, _abi, device, ctx = env
+    reqs = synth.serving_requests(60, seed=5)
+    frames = [synth.request_frame(r) for r in reqs]
+    pxs = [device.upload(f) for f in frames]
+    cubes = [device.cube_tensor(f.radar) for f in frames]
+    rng = np.random.default_rng(55)
+    gaps = rng.exponential(0.004, size=len(reqs))  # mean 4 ms between arrivals
+    srv = _abi.rsim_server_create(ctx.h, slots=3, express_slots=5)
+    try:
+        tickets = []
+        for r, f, px, cb, gap in zip(reqs, frames, pxs, cubes, gaps):
+            tickets.append(_abi.rsim_server_submit(srv, _abi.make_request(f.radar, px, _abi.TIERS[r["tier"]], cb)))
+            time.sleep(float(gap))
+        for t in tickets:
+            assert _abi.rsim_server_wait(srv, t, 120000) == _abi.OK, _abi.last_error()
+        st = _abi.rsim_server_stats_get(srv)
+    finally:
+        _abi.rsim_server_destroy(srv)
+    assert st.completed == len(reqs) and st.failed == 0
+    assert st.peak_in_flight >= 2
+    sample = rng.choice(len(reqs), size=max(1, len(reqs) // 20), replace=False)
+    for i in sample:
+        r, f = reqs[i], frames[i]
+        V, Ns, L = f.radar.V, f.radar.Ns, f.radar.L
+        ent = np.stack([rng.integers(0, V, 32), rng.integers(0, Ns, 32), rng.integers(0, L, 32)], axis=1)
+        ref = oracle.cube_entries(f.radar, f.pixels, ent)
+        got = cubes[i].cpu().numpy()[ent[:, 0], ent[:, 1], ent[:, 2]]
+        err = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        print(f"request {i}: M={f.radar.M} N={f.radar.N} Ns={Ns} L={L} grid={r['grid']} {r['tier']}: {err:.3e}")
+        assert err <= TOL[r["tier"]], (i, r["tier"], err)
+
+
 def test_server_admission_respects_budget(env):
     torch, _abi, device, ctx = env
     reqs = _requests(8, seed=9)
