@@ -164,7 +164,7 @@ extern "C" rsim_status rsim_measure_smem_atomics(rsim_ctx* ctx, double* lane_ops
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
-  // the context's status allocation holds 256 bytes; word 32 onwards is spare
+  // the probe's word of the context's status allocation
   unsigned* sink = ctx->status_dev + 32;
   const int blocks = 4 * std::max(ctx->num_sms, 1);
   cudaEvent_t a, b;
@@ -201,7 +201,7 @@ extern "C" rsim_status rsim_measure_mma_rate(rsim_ctx* ctx, double* flops_per_s,
   cudaError_t e = cudaSetDevice(ctx->device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
   cudaStream_t st = (cudaStream_t)stream;
-  unsigned* err = ctx->status_dev + 33;  // spare words of the status allocation
+  unsigned* err = ctx->status_dev + 33;  // the probe's word of the status allocation
   e = cudaFuncSetAttribute(mma_rate_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, kMmaProbeSmem);
   if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
   e = cudaMemsetAsync(err, 0, sizeof(unsigned), st);

@@ -19,6 +19,9 @@ struct rsim_ctx {
   size_t budget = 0;
   void* ws = nullptr;
   size_t ws_bytes = 0;
+  // 256 bytes: word 0 is the status word of the context's own calls (rsim_sync_status);
+  // word 32 is the shared-atomic probe's sink and word 33 the tensor-core probe's wait
+  // failures (measure.cu); the rest is unused
   unsigned* status_dev = nullptr;
   void* stage = nullptr;  // rsim_synth_host: device copies of the pixel arrays and the cube
   size_t stage_bytes = 0;
