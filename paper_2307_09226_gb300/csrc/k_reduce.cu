@@ -52,10 +52,13 @@ __global__ void split_reduce(const FrameIO* __restrict__ frames, int64_t count, 
 // cube = scale * sum over splits s = 0, 1, ... (in this order) of the tiled partial
 // sums, with compensated FP32 additions per component.  One thread per (accumulator
 // row, column pair) of a tile: the loads of consecutive threads are contiguous.  The
-// loads of kReduceBatch (8) splits are issued together; the additions keep the split
-// order.  (Sixteen at a time took 125 registers, halved the resident blocks and made the
-// reduction slower: 20.8 against 17.8 us on a 19-split frame.)
-__global__ void split_reduce_tiles(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles,
+// loads of kTileBatch (4) splits are issued together; the additions keep the split
+// order.  Four loads at a time fit 40 registers, so six blocks of 256 threads stay
+// resident per SM and a 256 x 256-pixel frame's 768 blocks run in one wave: with eight
+// (64 registers, four blocks per SM) the last 160 blocks ran as a second, quarter-full
+// wave (18.7 against 16.7 us).  Sixteen at a time took 125 registers and was slower still.
+constexpr int kTileBatch = 4;
+__global__ void __launch_bounds__(256, 6) split_reduce_tiles(const FrameIO* __restrict__ frames, Consts k, int NT, int ntiles,
                                    int64_t sstride, int splits, int out_dtype, int scale_mode) {
   wait_prior_grid();
   const FrameIO& fr = frames[blockIdx.y];
@@ -77,13 +80,13 @@ __global__ void split_reduce_tiles(const FrameIO* __restrict__ frames, Consts k,
     const int l = (int)(tile % ntiles) * NT + 2 * pr;
     if (row >= rows || l >= k.L) continue;
     float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, c3 = 0.f;
-    for (int b = 0; b < splits; b += kReduceBatch) {
-      float4 p[kReduceBatch];
+    for (int b = 0; b < splits; b += kTileBatch) {
+      float4 p[kTileBatch];
 #pragma unroll
-      for (int j = 0; j < kReduceBatch; ++j)
+      for (int j = 0; j < kTileBatch; ++j)
         p[j] = (b + j < splits) ? __ldcs(part + (int64_t)(b + j) * n4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < kReduceBatch; ++j) {
+      for (int j = 0; j < kTileBatch; ++j) {
         if (b + j < splits) {
           kahan_add(s0, c0, p[j].x);
           kahan_add(s1, c1, p[j].y);
@@ -124,9 +127,9 @@ cudaError_t launch_reduce_tiles(const Consts& k, const FrameIO* frames, int F, i
   const int64_t sstride = tensor_split_stride(k.V, k.Ns, k.L, nt);
   const int64_t n4 = sstride / 2;
   if (n4 <= 0 || F <= 0) return cudaSuccess;
-  // one wave of resident blocks (8 x 256 threads per SM) over all frames, grid-stride
+  // at most one wave of resident blocks (6 x 256 threads per SM) over all frames, grid-stride
   int64_t blocks = (n4 + 255) / 256;
-  const int64_t wave = std::max<int64_t>(1, 8ll * num_sms / F);
+  const int64_t wave = std::max<int64_t>(1, 6ll * num_sms / F);
   if (blocks > wave) blocks = wave;
   return launch_dependent(split_reduce_tiles, dim3((unsigned)blocks, F), dim3(256), 0, st, frames, k, nt,
                           (k.L + nt - 1) / nt, sstride, splits, out_dtype, scale_from_meta ? 1 : 0);
