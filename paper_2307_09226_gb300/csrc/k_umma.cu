@@ -843,11 +843,12 @@ cudaError_t launch_t(const Consts& k, const FrameIO* frames, Geo g, int grid, in
                      cudaStream_t st, cudaEvent_t mid) {
   cudaError_t e;
   if (nch_max > 0) {
-    // one wave of resident blocks (8 x 256 threads per SM), looping over the chunk images
+    // the phase blocks come first (one valid pixel per thread), then one image block per
+    // chunk image (up to 64 per SM, looping beyond): the block scheduler then balances the
+    // SMs, where a wave of 8 per SM left some blocks a second image at the end
     const int64_t items = (int64_t)g.F * g.ntiles * nch_max;
-    // the phase blocks come first (one valid pixel per thread), then the image blocks
     const int ph_blocks = fast_dtype >= 0 ? (int)((nch_max * kChunkPx + 255) / 256) : 0;
-    const int64_t blocks = std::min<int64_t>(items, 8ll * num_sms) + (int64_t)g.F * ph_blocks;
+    const int64_t blocks = std::min<int64_t>(items, 64ll * num_sms) + (int64_t)g.F * ph_blocks;
     if (blocks > 0x7FFFFFFF) return cudaErrorInvalidValue;
     e = launch_dependent(build_b_images<BF, SPLIT>, dim3((unsigned)blocks), dim3(256), 0, st, frames, k, g.NT,
                          g.ntiles, nch_max, g.F, scaled, fast_dtype, ph_blocks);
