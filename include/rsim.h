@@ -36,6 +36,12 @@
  *  - One rsim_ctx must not be used by two host threads at once, and work enqueued
  *    through it on one stream must complete before it is reused on another (its
  *    workspace is shared).  Use one context per stream, or the server below.
+ *  - rsim_synth and rsim_synth_host may be captured into a CUDA graph (stream
+ *    capture) once an uncaptured call of the same shape and tier has sized the
+ *    context's workspace (and, for rsim_synth_host, its staging buffer): the captured
+ *    call allocates nothing.  The graph holds those buffers' addresses, so a later call
+ *    on the context that grows them frees the memory the graph uses; a graph must not be
+ *    replayed after such a call.  A replay runs the whole call (every kernel) again.
  */
 #ifndef RSIM_H_
 #define RSIM_H_

@@ -287,3 +287,35 @@ def test_tensor_core_rate_probe(ctx):
     rate = _abi.rsim_measure_mma_rate(ctx.h)
     print(f"tensor-core MMA rate: {rate / 1e12:.1f} TFLOP/s")
     assert 1e15 < rate < 1.1 * 152 * (2 * 128 * 256 * 16 / 128) * 2.1e9
+
+
+@pytest.mark.parametrize("tier", ["split_fp16", "fp32"])
+def test_cuda_graph_capture_replays_the_call(ctx, tier):
+    """rsim_synth and rsim_synth_host captured into a CUDA graph (after an uncaptured call
+    sized the workspace) allocate nothing while captured, and every replay gives the same
+    bits as the plain call."""
+    torch = pytest.importorskip("torch")
+    device = _dev()
+    f = synth.parity_frame(seed=71, M=2, N=4, Ns=64, L=48, n_az=40, n_el=30)
+    px = device.upload(f)
+    plain = ctx.synth(f.radar, px, tier).cpu().numpy()
+    host = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+            for k, a in zip(device.FIELDS, f.pixels.arrays())}
+    out_host = device.cube_tensor(f.radar, device="cpu").pin_memory()
+    ctx.synth_host(f.radar, host, tier, cube=out_host)  # sizes the staging buffer
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    cube = device.cube_tensor(f.radar)
+    g1, g2 = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g1, stream=s):
+        ctx.synth(f.radar, px, tier, cube=cube, stream=s)
+    with torch.cuda.graph(g2, stream=s):
+        ctx.synth_host(f.radar, host, tier, cube=out_host, stream=s)
+    for _ in range(2):
+        cube.zero_()
+        out_host.zero_()
+        g1.replay()
+        g2.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(cube.cpu().numpy(), plain)
+        assert np.array_equal(out_host.numpy(), plain)
