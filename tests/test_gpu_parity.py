@@ -183,16 +183,17 @@ def test_largest_serving_shape_normwise(ctx, tier, mask):
     assert err <= TOL[tier]
 
 
-def test_empty_and_all_masked_frames_give_zero(ctx):
+@pytest.mark.parametrize("tier", ALL_TIERS)
+def test_empty_and_all_masked_frames_give_zero(ctx, tier):
     radar = Radar(M=2, N=2, Ns=16, L=8)
     px = synth.random_frame(radar, 40, 40, seed=1, mask_frac=1.0)
-    got = _run(ctx, synth.Frame(radar, px, "complex64"), "fp32")
+    got = _run_or_skip(ctx, synth.Frame(radar, px, "complex64"), tier)
     assert not np.any(got)
     from paper_2307_09226_gb300 import _abi
     import torch
     empty = {k: torch.zeros(0, dtype=torch.float32, device="cuda") for k in _dev().FIELDS}
     cube = torch.full((4, 16, 8), 7.0, dtype=torch.complex64, device="cuda")
-    _abi.rsim_synth(ctx.h, radar, empty, _abi.TIER_FP32, cube)
+    _abi.rsim_synth(ctx.h, radar, empty, _abi.TIERS[tier], cube)
     assert ctx.sync_status() == _abi.OK
     assert not torch.any(cube != 0)
 
@@ -264,7 +265,7 @@ def test_point_target_fft_peaks_on_gpu(ctx):
     assert (kr, kd) == (k_r, (-k_d) % r.L)
 
 
-@pytest.mark.parametrize("tier", ["fp32", "split_fp16", "split_bf16"])
+@pytest.mark.parametrize("tier", ["fp32", "split_fp16", "split_bf16", "bf16", "nufft"])
 def test_tdm_motion_flag(ctx, tier):
     """RSIM_FLAG_TDM_MOTION adds -f_D m T_b per Tx slot; parity with the oracle."""
     from dataclasses import replace
