@@ -68,6 +68,26 @@ def test_batch_with_uneven_pixel_counts(env):
             assert err <= TOL[tier], (tier, err)
 
 
+@pytest.mark.parametrize("tier", ["split_fp16", "bf16", "nufft"])
+def test_batch_of_fp64_frames(env, tier):
+    """A batch of FP64 pixel buffers of one size with uneven valid counts (the tensor tiers'
+    operand builder computes every frame's fast-time phases from the FP64 fields): each
+    frame is bit-identical to its alone result (equal pixel counts share a plan) and within
+    its tier's tolerance of the oracle."""
+    torch, _abi, device, ctx = env
+    radar = Radar(M=2, N=4, Ns=96, L=40)
+    frames = [synth.random_frame(radar, 60, 45, seed=s, mask_frac=m, dtype=np.float64)
+              for s, m in [(11, 0.2), (12, 0.9), (13, 0.0)]]
+    pxs = [device.upload(p) for p in frames]
+    cubes = ctx.synth_batch(radar, pxs, tier)
+    assert ctx.sync_status() == _abi.OK
+    for p, px, cb in zip(frames, pxs, cubes):
+        got = cb.cpu().numpy()
+        assert np.array_equal(got, ctx.synth(radar, px, tier).cpu().numpy())
+        err = oracle.rel_l2(got, oracle.cube_separable(radar, p))
+        assert err <= TOL[tier], (tier, err)
+
+
 def _requests(n, seed=5):
     reqs = synth.serving_requests(n, seed=seed, grids=(32, 48, 64),
                                   tiers=("fp32", "split_bf16", "split_fp16", "nufft"))
