@@ -32,6 +32,8 @@ def env():
     ("fp32", lambda: synth.parity_frame(seed=40, M=2, N=4, Ns=128, L=64, n_az=128, n_el=128)),
     ("split_fp16", lambda: synth.parity_frame(seed=41, M=3, N=4, Ns=128, L=64, n_az=90, n_el=80)),
     ("split_bf16", lambda: synth.parity_frame(seed=42, M=2, N=3, Ns=96, L=48, n_az=71, n_el=70)),
+    ("split_fp16", lambda: synth.parity_frame(seed=43, M=2, N=4, Ns=64, L=40, n_az=50, n_el=45,
+                                              dtype=np.float64)),
 ])
 def test_static_entry_matches_rsim_synth_twice(env, tier, maker):
     torch, _abi, device, ctx = env
