@@ -15,8 +15,9 @@
 // kernel writes it once per frame as ready-made shared-memory images: for each
 // 32-pixel chunk, 2 NT rows of 128 B in the 128-byte-swizzled K-major layout the MMA
 // reads.  Blocks of the same kernel compute the frame's FP64 fast-time and channel
-// phases (which A is made from) beside the image blocks.  A (fast-time/channel phasors) differs for every row tile and is never
-// reused, so it is generated on chip and never touches HBM.
+// phases (which A is made from) beside the image blocks.  A (fast-time/channel
+// phasors) differs for every row tile and is never reused, so it is generated on chip
+// and never touches HBM.
 //
 // The contraction runs one persistent CTA per SM, warp-specialised:
 //   warps 0-15  produce A for a 128-row tile straight into tensor memory (one row per
