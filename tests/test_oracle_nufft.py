@@ -65,3 +65,18 @@ def test_grid_size_is_the_oversampled_power_of_two():
     """G = the smallest power of two >= 2 N, and at least 16 cells."""
     assert [nu.grid_size(n) for n in (4, 7, 8, 9, 64, 65, 128, 129, 2048)] == \
         [16, 16, 16, 32, 128, 256, 256, 512, 4096]
+
+
+@pytest.mark.parametrize("beta", [2.3, 9.0, 14.4])
+def test_es_kernel_special_values(beta):
+    """The exponential-of-semicircle kernel at points where it has a closed form: 1 at the
+    centre, e^-beta at the support's edge, e^(-beta/2) where sqrt(1 - z^2) = 1/2, zero
+    outside [-1, 1]; it is even and falls monotonically from the centre to the edge."""
+    z = np.array([0.0, 1.0, -1.0, np.sqrt(3.0) / 2.0, -np.sqrt(3.0) / 2.0, 0.6])
+    want = np.exp(-beta * np.array([0.0, 1.0, 1.0, 0.5, 0.5, 0.2]))
+    np.testing.assert_allclose(nu.es_kernel(z, beta), want, rtol=1e-14)
+    assert np.all(nu.es_kernel(np.array([1.0 + 1e-12, -1.5, 7.0]), beta) == 0.0)
+    t = np.linspace(0.0, 1.0, 101)
+    f = nu.es_kernel(t, beta)
+    np.testing.assert_array_equal(f, nu.es_kernel(-t, beta))
+    assert np.all(np.diff(f) < 0)

@@ -179,3 +179,53 @@ def test_misses_are_background():
     o = rc.raycast([_sphere((0, -5.0, 0), 1.0)], 16, 8, *FOV)  # behind the radar
     assert np.all(np.isinf(o["range"])) and np.all(o["sigma_re"] == 0) and np.all(o["vel"] == 0)
     assert np.all(o["prim"] == -1)
+
+
+def test_hit_plane_parallelogram_by_hand():
+    """Distances to parallelograms worked out by hand: an axis-aligned square in the plane
+    y = 3 and a skewed parallelogram (b and c not orthogonal) in y = 4, hit at chosen
+    (s, u) coordinates; points outside the edges, parallel rays and rays pointing away
+    miss.  The skewed case fails if the 2x2 Gram solve swaps or transposes its terms."""
+    sq = synth._prim("plane", (-1.0, 3.0, -1.0), (2.0, 0.0, 0.0), (0.0, 0.0, 2.0))
+    sk = synth._prim("plane", (0.0, 4.0, 0.0), (1.0, 0.0, 0.0), (1.0, 0.0, 1.0))
+
+    def unit(v):
+        v = np.asarray(v, float)
+        return v / np.linalg.norm(v)
+
+    pts_sq = [(0.0, 3.0, 0.0), (0.5, 3.0, -0.7), (0.9, 3.0, 0.9)]
+    d = np.stack([unit(p) for p in pts_sq])
+    np.testing.assert_allclose(rc.hit_plane(d, sq), [np.linalg.norm(p) for p in pts_sq], rtol=1e-14)
+    # skewed: a + s b + u c for (s, u) inside and outside the unit square
+    a, b, c = np.array([0.0, 4.0, 0.0]), np.array([1.0, 0.0, 0.0]), np.array([1.0, 0.0, 1.0])
+    inside = [a + 0.3 * b + 0.6 * c, a + 0.9 * b + 0.1 * c]
+    outside = [a + 1.2 * b + 0.3 * c, a + 0.2 * b - 0.1 * c, a + 0.5 * b + 1.1 * c]
+    d_in = np.stack([unit(p) for p in inside])
+    np.testing.assert_allclose(rc.hit_plane(d_in, sk), [np.linalg.norm(p) for p in inside], rtol=1e-14)
+    d_out = np.stack([unit(p) for p in outside])
+    assert np.all(np.isinf(rc.hit_plane(d_out, sk)))
+    # parallel to the plane, and pointing away from it
+    d_miss = np.stack([unit((1.0, 0.0, 0.0)), unit((0.0, -1.0, 0.0)), unit((0.1, -3.0, 0.2))])
+    assert np.all(np.isinf(rc.hit_plane(d_miss, sq)))
+
+
+def test_raycast_angles_closed_form_and_grid_agreement():
+    """A large plane y = 5 seen at arbitrary angles: range 5 / (cos el cos az) and the
+    Lambert strength rho cos(incidence) / R^2 (rho cos(incidence) without fall-off), the
+    incidence angle's cosine being the ray's y component; the angle form agrees exactly
+    with the grid form at the grid's own angles."""
+    wall = synth._prim("plane", (-50.0, 5.0, -50.0), (100.0, 0.0, 0.0), (0.0, 0.0, 100.0), rho=0.7)
+    az = np.array([0.0, 0.3, -0.7, 1.1])
+    el = np.array([0.0, -0.2, 0.4, 0.1])
+    out = rc.raycast_angles([wall], az, el)
+    cosi = np.cos(el) * np.cos(az)
+    R = 5.0 / cosi
+    np.testing.assert_allclose(out["range"], R, rtol=1e-13)
+    np.testing.assert_allclose(out["sigma_re"], 0.7 * cosi / R ** 2, rtol=1e-12)
+    flat = rc.raycast_angles([wall], az, el, falloff=False)
+    np.testing.assert_allclose(flat["sigma_re"], 0.7 * cosi, rtol=1e-12)
+    scene = synth.random_scene(3)
+    grid = rc.raycast(scene, 17, 9, *synth.CAMERA_FOV)
+    again = rc.raycast_angles(scene, grid["az"], grid["el"])
+    for k in ("range", "sigma_re", "vel"):
+        np.testing.assert_array_equal(grid[k], again[k])
