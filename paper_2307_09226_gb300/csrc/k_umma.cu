@@ -149,7 +149,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
 // L2 eviction priorities.  A chunk's B images are read by every row tile at about the
 // same time and then never again, while the split partial sums wait in L2 for the
 // reduction after the contraction: the B copies take evict_first and the partial-sum
-// stores and reductions evict_last, so the streaming images do not push the partials out.
+// stores and reductions evict_last.  (The partial sums are found in L2 by the reduction
+// with evict_normal stores too; what it pays for is reading lines that SMs of the other
+// die wrote, over the link between the two dies' L2 partitions.)
 // bulk_g2s with a createpolicy policy for the source lines:
 __device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
                                               uint64_t policy) {
