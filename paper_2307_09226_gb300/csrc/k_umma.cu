@@ -150,8 +150,8 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
 // same time and then never again, while the split partial sums wait in L2 for the
 // reduction after the contraction: the B copies take evict_first and the partial-sum
 // stores and reductions evict_last.  (The partial sums are found in L2 by the reduction
-// with evict_normal stores too; what it pays for is reading lines that SMs of the other
-// die wrote, over the link between the two dies' L2 partitions.)
+// with evict_normal stores too; what it pays for is that most of its reads are served by
+// the other die's L2 partition, over the link between the two partitions.)
 // bulk_g2s with a createpolicy policy for the source lines:
 __device__ __forceinline__ void bulk_g2s_hint(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
                                               uint64_t policy) {
