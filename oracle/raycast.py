@@ -77,7 +77,7 @@ def hit_plane(d, prim):
     dn = d @ n
     with np.errstate(invalid="ignore", divide="ignore"):
         t = np.where(dn != 0, (a @ n) / dn, INF)
-    x = d * t[:, None] - a
+        x = d * t[:, None] - a  # NaN on rays parallel to the plane: dropped below
     # coordinates (s, t) of x in the basis (b, c): solve the 2x2 Gram system
     bb, cc, bc = b @ b, c @ c, b @ c
     det = bb * cc - bc * bc
