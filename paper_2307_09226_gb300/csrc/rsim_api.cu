@@ -285,11 +285,12 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
     }
     for (int i = 0; i < kProfEvents; ++i) ev[i] = ctx->ev_pool[base + i];
     ctx->prof_calls++;
-    // compaction + phases (2); FP32: direct sum (1); tensor tiers: operand builder (1 when
-    // a frame has valid pixels), frame order (1 for a batch), contraction (1); NUFFT: the
-    // NUFFT kernels of each frame; the split reduction (1 when the partial buffer is used)
+    // compaction + phases (counted when launched: one cooperative kernel or two); FP32:
+    // direct sum (1); tensor tiers: operand builder (1 when a frame has valid pixels), frame
+    // order (1 for a batch), contraction (1); NUFFT: the NUFFT kernels of each frame; the
+    // split reduction (1 when the partial buffer is used)
     const bool tensor = tensor_tier(tier);
-    ctx->prof_kernels += 2 + (tier == RSIM_TIER_NUFFT ? kNufftKernels * F
+    ctx->prof_kernels += (tier == RSIM_TIER_NUFFT ? kNufftKernels * F
                               : tensor ? 1 + (mp > 0 ? 1 : 0) + (F > 1 ? 1 : 0) : 1) + (use_partial ? 1 : 0);
     cudaEventRecord(ev[0], st);
   }
@@ -298,8 +299,10 @@ rsim_status run_frames(rsim_ctx* ctx, char* ws, size_t ws_bytes, const Consts& k
   const bool defer = tensor_tier(tier);
   {
     NvtxRange r(defer ? "compaction + slow-time phases" : "compaction + FP64 phases");
+    int launched = 0;
     e = launch_prep(k, table, F == 1 ? host.data() : nullptr, F, mp, frames[0].dtype, false, defer, status,
-                    counter, st);
+                    counter, st, true, &launched);
+    if (prof) ctx->prof_kernels += launched;
   }
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (prof) cudaEventRecord(ev[1], st);

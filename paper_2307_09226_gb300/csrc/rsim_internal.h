@@ -269,7 +269,7 @@ inline size_t bimg_part_bytes(int nt) { return (size_t)2 * nt * 128; }
 // channel phases (phA, phC) are left to the tensor tiers' operand builder.
 cudaError_t launch_prep(const Consts& k, FrameIO* frames, const FrameIO* one, int F, int64_t maxP,
                         int dtype, bool write_idx_only, bool defer_fast_terms, unsigned* status, int* counter,
-                        cudaStream_t st);
+                        cudaStream_t st, bool cooperative = true, int* launched = nullptr);
 // tile_n: n values per CTA tile (64 or 128).
 cudaError_t launch_direct(const Consts& k, const FrameIO* frames, int F, int splits, int tile_n,
                           int out_dtype, cudaStream_t st);

@@ -126,7 +126,7 @@ extern "C" rsim_status rsim_synth_static(const rsim_radar_params* params, const 
   if (e != cudaSuccess) return cuda_fail(e, "static workspace set-up");
 
   const bool defer = tensor_tier(tier);  // the operand builder computes the fast-time phases
-  e = launch_prep(k, table, &io, 1, P, pixels->dtype, false, defer, status, counter, st);
+  e = launch_prep(k, table, &io, 1, P, pixels->dtype, false, defer, status, counter, st, false);
   if (e != cudaSuccess) return cuda_fail(e, "prep kernels");
   if (tier == RSIM_TIER_FP32) {
     e = launch_direct(k, table, 1, splits, plan.tile_n, out_dtype, st);

@@ -58,7 +58,8 @@ def test_static_entry_matches_rsim_synth_twice(env, tier, maker):
     for got in outs:
         assert np.all(np.isfinite(got))
         assert oracle.rel_l2(got, ref) <= TOL[tier]
-    # same plan, same kernels: the results are identical, call after call
+    # same plan: the results are identical, call after call (the static entry compacts the
+    # pixels with the two-kernel form, the context with the cooperative one)
     assert np.array_equal(outs[0], ref) and np.array_equal(outs[1], ref)
 
 
